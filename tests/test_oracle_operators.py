@@ -1,0 +1,155 @@
+"""Pins of the oracle's discrete operators (Appendix B, Section 2.2).
+
+* The assembled line matrices (I + tau/2 D_d) reproduce the operator D_d applied
+  as a stencil to whole fields (two separate codings of the same rows).
+* The split sum D_r + D_theta + D_phi + D_M applied to a smooth field converges
+  at second order to the continuous operator of eqs. (nonconservmass)-
+  (nonconserveos), computed independently through Cartesian coordinates
+  (inputs/continuous.py).  Interior points only: the wall closures are pinned
+  by the convergence tests of the full scheme.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from inputs import Grid, Params, sample, sample_walls
+
+sympy = pytest.importorskip("sympy")
+
+
+def _zero_boundary(g, V):
+    V = [v.copy() for v in V]
+    V[1][0] = 0
+    V[1][-1] = 0
+    V[2][:, 0] = 0
+    V[2][:, -1] = 0
+    if not g.periodic:
+        V[3][:, :, 0] = 0
+        V[3][:, :, -1] = 0
+    return V
+
+
+def _case(periodic):
+    if periodic:
+        g = Grid(6, 7, 9, 1.0, 2.0, 0.5, 2.6, 0.0, 2 * np.pi, periodic=True)
+    else:
+        g = Grid(6, 7, 9, 1.0, 2.0, np.pi / 4, 3 * np.pi / 4, np.pi / 4, 7 * np.pi / 4)
+    par = Params(gamma=1.6, cv=1.0, Pr=1.0, mu=0.3, omega=0.2, g=0.5, pinf=3.0)
+    rng = np.random.default_rng(5)
+    U = [rng.standard_normal(s) for s in g.shapes()]
+    U[0] = 50.0 + U[0]
+    U[4] = 80.0 + U[4]
+    return g, par, U
+
+
+def _line_vec(g, V, d, kind, a, b):
+    """unknowns of one line in solver order"""
+    n = [g.nr, g.nt, g.np][d]
+    cyc = g.periodic and d == 2
+    if kind == 0:
+        x = np.zeros((n, 3))
+        for m in range(n):
+            idx = [a, b]
+            idx.insert(d, m)
+            i, j, k = idx
+            x[m, 0] = V[0][i, j, k]
+            x[m, 1] = V[4][i, j, k]
+            if m < n - 1 or cyc:
+                f = [i, j, k]
+                f[d] = (m + 1) % n if cyc else m + 1
+                x[m, 2] = V[1 + d][tuple(f)]
+        return x
+    cc = {0: (1, 2), 1: (0, 2), 2: (0, 1)}[d][kind - 1]
+    x = np.zeros(n)
+    for m in range(n):
+        idx = [a, b]
+        idx.insert(d, m)
+        x[m] = V[1 + cc][tuple(idx)]
+    return x
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_assembly_matches_operator(periodic, d):
+    g, par, U = _case(periodic)
+    rng = np.random.default_rng(17 + d)
+    V = _zero_boundary(g, [rng.standard_normal(s) for s in g.shapes()])
+    DV = oracle.apply_op(g, par, U, d, V)
+    tau = 0.1
+    cyc = periodic and d == 2
+    lines = {0: [(2, 3), (0, 0), (6, 8) if d != 2 else (5, 6)]}
+    for kind in (0, 1, 2):
+        for (a, b) in ([(2, 3), (0, 0)] if kind == 0 else [(1, 1), (1, 2)]):
+            if kind == 0 and d == 0 and a >= g.nt:
+                continue
+            A, B, C = oracle.line_system(g, par, U, d, kind, a, b, tau)
+            x = _line_vec(g, V, d, kind, a, b)
+            y = _line_vec(g, DV, d, kind, a, b)
+            n = len(x)
+            if kind == 0:
+                Mx = np.einsum("mij,mj->mi", B, x)
+                Mx[1:] += np.einsum("mij,mj->mi", A[1:], x[:-1])
+                Mx[:-1] += np.einsum("mij,mj->mi", C[:-1], x[1:])
+                if cyc:
+                    Mx[0] += A[0] @ x[-1]
+                    Mx[-1] += C[-1] @ x[0]
+                got = (Mx - x) * (2.0 / tau)
+                if not cyc:
+                    got[-1, 2] = y[-1, 2] = 0.0   # wall face: identity row, no operator row
+            else:
+                Mx = B * x
+                Mx[1:] += A[1:] * x[:-1]
+                Mx[:-1] += C[:-1] * x[1:]
+                if cyc:
+                    Mx[0] += A[0] * x[-1]
+                    Mx[-1] += C[-1] * x[0]
+                got = (Mx - x) * (2.0 / tau)
+            scale = np.max(np.abs(y)) + 1e-300
+            assert np.max(np.abs(got - y)) <= 1e-11 * scale, (kind, a, b)
+
+
+def _smooth_fields(periodic):
+    """Smooth analytic fields (sympy) with all velocity components and gradients active."""
+    from inputs.continuous import r, th, ph
+    s, c = sympy.sin, sympy.cos
+    p = 40 + s(2 * r) * c(th) * (1 + c(ph) / 2) + r
+    ur = s(3 * r) * s(th) ** 2 * (1 + s(ph)) / 3 + 0.2
+    ut = c(2 * r) * s(2 * th) * c(ph) / 2 - 0.1
+    up = (r * s(th) + c(r) * c(th) * s(2 * ph)) / 2
+    T = 60 + c(r) * s(th) * (1 + s(2 * ph) / 3)
+    return [p, ur, ut, up, T]
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_split_sum_converges_to_continuous_operator(periodic):
+    from inputs.continuous import operator, lambdify
+    par = Params(gamma=1.4, cv=2.5, Pr=0.8, mu=0.8, pinf=5.0, g=0.7, omega=0.3)
+    exprs = _smooth_fields(periodic)
+    N = operator(*exprs, gamma=par.gamma, cv=par.cv, Pr=par.Pr, mu=par.mu, pinf=par.pinf,
+                 g=par.g, omega=par.omega)
+    fex = lambdify(exprs)
+    fN = lambdify(N)
+    errs = []
+    for n in (8, 16, 32):
+        if periodic:
+            g = Grid(n, n, 2 * n, 1.0, 2.0, 0.6, 2.5, 0.0, 2 * math.pi, periodic=True)
+        else:
+            g = Grid(n, n, n, 1.0, 2.0, 0.6, 2.5, 0.3, 2.2)
+        U = sample(fex, g)
+        walls = sample_walls(fex[1:4], g)
+        tot = [np.zeros(s) for s in g.shapes()]
+        for which in range(4):
+            out = oracle.apply_op(g, par, U, which, U, ubar_walls=walls, v_walls=walls)
+            for q in range(5):
+                tot[q] += out[q]
+        tot[1] += par.g   # G
+        ref = sample(fN, g)
+        m = n // 8 * 2    # stay two coarse cells away from every wall
+        sl = (slice(m, -m), slice(m, -m), slice(m, -m) if not periodic else slice(None))
+        errs.append([np.max(np.abs((tot[q] - ref[q])[sl])) / np.max(np.abs(ref[q])) for q in range(5)])
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(errs[-1] < 2e-3), errs
+    assert np.all((rates > 1.85) & (rates < 2.3)), (errs, rates)
