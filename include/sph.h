@@ -1,0 +1,133 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) library for the direction-splitting
+ * scheme of Frolov, Minev & Takhirov, "An efficient algorithm for weakly
+ * compressible flows in spherical geometries" (arXiv 2004.13887).
+ *
+ * The library advances the non-conservative compressible Navier-Stokes system
+ * of Section 2.1 (eqs. nonconservmass-nonconserveos) in a spherical sector by
+ * the Picard-iterated, direction-split Crank-Nicolson scheme of Section 2.2
+ * (eqs. chapter3mainsd, splitting2, spl1-spl3) on the MAC grid.
+ *
+ * Conventions (all calls):
+ *  - Unknowns U = [p, u_r, u_theta, u_phi, T] (Section 2.1).  p and T are
+ *    stored as perturbations p' = p - p_ref(r), T' = T - T_ref(r) about a radial
+ *    background (the "a priori" pressure rescaling of Section 3.1).
+ *  - Layout: FP64, C order, phi fastest.  Field f has sph_field_size(grid, f)
+ *    elements:  p, T: nr*nt*np (centres); u_r: (nr+1)*nt*np (r-faces);
+ *    u_theta: nr*(nt+1)*np (theta-faces); u_phi: nr*nt*npf (phi-faces) with
+ *    npf = np+1, or np when phi is periodic.
+ *  - Boundary conditions: u = 0 tangentially on every wall (no-slip; ghost =
+ *    -interior), the normal velocity on wall faces is whatever the state holds
+ *    there and is not changed by sph_step; zero normal derivative of p' and T';
+ *    optional periodic phi (cyclic line systems).
+ *  - Pointers marked "device" are CUDA device pointers of the current device;
+ *    "host" pointers are ordinary host memory.  The library never keeps a
+ *    caller pointer after a call returns.
+ *  - All work is queued on the stream given to sph_create; calls that return
+ *    data to host memory synchronise that stream.
+ *  - Return value: SPH_OK (0) or a negative SPH_ERR_* code; sph_strerror()
+ *    describes it.  After SPH_ERR_CUDA the context should be destroyed.
+ */
+#ifndef SPH_H
+#define SPH_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPH_OK 0
+#define SPH_ERR_ARG (-1)        /* bad argument (sizes, pointers, dt <= 0, ...) */
+#define SPH_ERR_CUDA (-2)       /* a CUDA runtime call failed */
+#define SPH_ERR_NONFINITE (-3)  /* NaN/Inf in the new state; the state is left at U^n */
+#define SPH_ERR_SINGULAR (-4)   /* a zero pivot in a line solve; state left at U^n */
+#define SPH_ERR_NOMEM (-5)      /* device allocation failed */
+
+#define SPH_PREC_FP64 0          /* every step in FP64 */
+#define SPH_PREC_MIXED 1         /* FP32 bulk stencils/line solves, FP64 iterate */
+
+/* Domain [r1,r2] x [th1,th2] x [ph1,ph2] with nr x nth x nph uniform cells
+ * (Section 2.1, Omega).  periodic_phi != 0 requires ph2 - ph1 = 2 pi in the
+ * intended use (not checked).  th1 >= 0, th2 <= pi; a pole face is allowed. */
+typedef struct {
+  int nr, nth, nph;
+  double r1, r2, th1, th2, ph1, ph2;
+  int periodic_phi;
+} sph_grid;
+
+/* Material constants (Section 2.1): gamma = cp/cv, kappa = mu*cp/Pr, stiffened-gas
+ * pi_inf, gravity g along e_r on the left-hand side (eq. nonconservmom),
+ * rotation omega about the polar axis.  precision: SPH_PREC_*. */
+typedef struct {
+  double gamma, cv, Pr, mu, pi_inf, g, omega;
+  int precision;
+} sph_params;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Number of elements of field f (0..4) for a grid. */
+size_t sph_field_size(const sph_grid* grid, int f);
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
+ * legacy default stream).  The context owns all device buffers (state U^n,
+ * iterate U^{n+1,k}, coefficients, right-hand sides, line-solve scratch).
+ * Errors: SPH_ERR_ARG (nr, nth, nph < 2; r1 <= 0; empty ranges; periodic with
+ * nph < 3), SPH_ERR_NOMEM, SPH_ERR_CUDA. */
+int sph_create(const sph_grid* grid, const sph_params* params, void* stream, sph_ctx** out);
+
+/* Radial background (Section 3.2 hydrostatic state, or a constant): host arrays
+ * of nr+2 values each, index 0 the ghost below r1 and nr+1 the ghost above r2.
+ * NULL sets that background to zero (the default). */
+int sph_set_background(sph_ctx* ctx, const double* p_ref, const double* T_ref);
+
+/* Copy the 5 fields in (host or device per on_device) into U^n. */
+int sph_set_state(sph_ctx* ctx, const double* const* fields, int on_device);
+
+/* Copy U^n out into the 5 caller arrays (host or device per on_device). */
+int sph_get_state(sph_ctx* ctx, double* const* fields, int on_device);
+
+/* One time step t^n -> t^{n+1} (eq. splitting2 iterated n_iter = K times, each
+ * iteration one right-hand side and the three sweeps spl1-spl3).
+ * source: NULL or 5 arrays (host or device per source_on_device) holding the
+ * forcing S at t^{n+1/2} of dU/dt + N(U) + G = S.  residual_out: NULL or 5 host
+ * doubles, the RMS over unknowns of the last increment U^{k+1}-U^k per field
+ * (synchronises).  On SPH_ERR_NONFINITE / SPH_ERR_SINGULAR U^n is unchanged. */
+int sph_step(sph_ctx* ctx, double dt, int n_iter, const double* const* source, int source_on_device,
+             double* residual_out);
+
+/* Stage entry points (the same kernels sph_step runs), for testing each part.
+ * sph_set_iterate: copy 5 fields into the iterate U^{n+1,k} (default: U^n).
+ * sph_rhs: R = -(U^k - U^n) - dt [N(Ubar) + G - S], Ubar = (U^k + U^n)/2, the
+ *   right-hand side of eq. (spl1) in its midpoint form; R_out: 5 device arrays.
+ * sph_sweep: solve (I + dt/2 D_dir(Ubar)) x = rhs on every line of direction
+ *   dir (0 r, 1 theta, 2 phi; eqs. spl1-spl3); rhs, x: 5 device arrays each
+ *   (may not alias).  Values of rhs at wall faces are ignored; x is 0 there. */
+int sph_set_iterate(sph_ctx* ctx, const double* const* fields, int on_device);
+int sph_rhs(sph_ctx* ctx, double dt, const double* const* source, int source_on_device, double* const* R_out);
+int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double* const* x);
+
+/* Number of this library's kernel launches since creation (for accounting). */
+long long sph_launch_count(const sph_ctx* ctx);
+
+/* Per-kernel timing.  sph_profile(ctx, 1) clears the record and starts timing
+ * every launch with a pair of CUDA events on the context's stream; 0 stops.
+ * sph_profile_read synchronises the stream and writes, for each kernel kind
+ * SPH_K_* (SPH_NKERNELS entries), the summed duration in ms and the launch
+ * count (either pointer may be NULL).  At most 65536 launches are recorded;
+ * later ones are counted but not timed (returned count includes them). */
+#define SPH_K_AVG 0
+#define SPH_K_COEF 1
+#define SPH_K_RHS 2
+#define SPH_K_SWEEP_R 3
+#define SPH_K_SWEEP_TH 4
+#define SPH_K_SWEEP_PH 5
+#define SPH_NKERNELS 8
+int sph_profile(sph_ctx* ctx, int enable);
+int sph_profile_read(sph_ctx* ctx, double* ms, long long* count);
+
+void sph_destroy(sph_ctx* ctx);
+const char* sph_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -201,12 +201,22 @@ def bubble_grid(n=(128, 256, 256)) -> Grid:
                 math.pi - half, math.pi + half)
 
 
+def bubble_window(n=(128, 256, 256), width=(64, 64)) -> Grid:
+    """The central width[0] x width[1] columns of the bubble sector, same cells."""
+    g = bubble_grid(n)
+    tm, pm = 0.5 * (g.t1 + g.t2), 0.5 * (g.p1 + g.p2)
+    return Grid(g.nr, width[0], width[1], g.r1, g.r2, tm - 0.5 * width[0] * g.dth, tm + 0.5 * width[0] * g.dth,
+                pm - 0.5 * width[1] * g.dph, pm + 0.5 * width[1] * g.dph)
+
+
 def bubble(n=(128, 256, 256), seed: int = 1, dt: float = 1.0, steps: int = 200, K: int = 2,
-           amplitude: float = 0.5, radius: float = 2000.0, altitude: float = 2000.0, mu: float = None) -> Case:
+           amplitude: float = 0.5, radius: float = 2000.0, altitude: float = 2000.0, mu: float = None,
+           grid: Grid = None) -> Case:
     """Rising thermal bubble: Gaussian dTheta = A exp(-L^2), L = |x - x_c| / R,
     centre at the given altitude above the domain centre, centre altitude and
-    radius jittered by +-10 % (seeded)."""
-    grid = bubble_grid(n)
+    radius jittered by +-10 % (seeded).  grid: another grid (e.g. a central
+    window of the sector) to sample the same initial state on."""
+    grid = bubble_grid(n) if grid is None else grid
     rng = np.random.default_rng(seed)
     radius = radius * (1.0 + rng.uniform(-0.1, 0.1))
     altitude = altitude * (1.0 + rng.uniform(-0.1, 0.1))

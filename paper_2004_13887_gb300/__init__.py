@@ -1,0 +1,242 @@
+"""GB300 (sm_103a) implementation of the direction-splitting scheme for weakly
+compressible flow in spherical coordinates (Frolov, Minev & Takhirov,
+arXiv 2004.13887).
+
+A thin ctypes binding over the C ABI in include/sph.h (libsph.so, built in-tree
+by ``build()``).  Every step of the method runs in the library's CUDA kernels;
+this module only marshals arguments.  PyTorch supplies device memory and the
+stream.  There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import LIB, build
+
+__all__ = ["build", "load", "Solver", "SphError", "sph_field_size", "SPH_PREC_FP64", "SPH_PREC_MIXED"]
+
+SPH_PREC_FP64 = 0
+SPH_PREC_MIXED = 1
+
+_ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "non-finite state",
+           -4: "zero pivot in a line solve", -5: "device allocation failed"}
+
+
+class SphError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {_ERRORS.get(code, 'unknown')} ({code})")
+
+
+class sph_grid(C.Structure):
+    _fields_ = [("nr", C.c_int), ("nth", C.c_int), ("nph", C.c_int),
+                ("r1", C.c_double), ("r2", C.c_double), ("th1", C.c_double), ("th2", C.c_double),
+                ("ph1", C.c_double), ("ph2", C.c_double), ("periodic_phi", C.c_int)]
+
+
+class sph_params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cv", C.c_double), ("Pr", C.c_double), ("mu", C.c_double),
+                ("pi_inf", C.c_double), ("g", C.c_double), ("omega", C.c_double), ("precision", C.c_int)]
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+_PP = C.POINTER(_DP)
+_CTX = C.c_void_p
+
+# name -> (argtypes, restype); every symbol include/sph.h declares
+SIGNATURES = {
+    "sph_field_size": ([C.POINTER(sph_grid), C.c_int], C.c_size_t),
+    "sph_create": ([C.POINTER(sph_grid), C.POINTER(sph_params), C.c_void_p, C.POINTER(_CTX)], C.c_int),
+    "sph_set_background": ([_CTX, _DP, _DP], C.c_int),
+    "sph_set_state": ([_CTX, _PP, C.c_int], C.c_int),
+    "sph_get_state": ([_CTX, _PP, C.c_int], C.c_int),
+    "sph_step": ([_CTX, C.c_double, C.c_int, _PP, C.c_int, _DP], C.c_int),
+    "sph_set_iterate": ([_CTX, _PP, C.c_int], C.c_int),
+    "sph_rhs": ([_CTX, C.c_double, _PP, C.c_int, _PP], C.c_int),
+    "sph_sweep": ([_CTX, C.c_int, C.c_double, _PP, _PP], C.c_int),
+    "sph_launch_count": ([_CTX], C.c_longlong),
+    "sph_profile": ([_CTX, C.c_int], C.c_int),
+    "sph_profile_read": ([_CTX, _DP, C.POINTER(C.c_longlong)], C.c_int),
+    "sph_destroy": ([_CTX], None),
+    "sph_strerror": ([C.c_int], C.c_char_p),
+}
+
+
+def load(path: str = LIB):
+    """Load libsph.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2004_13887_gb300.build() (needs nvcc)")
+        L = C.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _grid_struct(grid) -> sph_grid:
+    return sph_grid(int(grid.nr), int(grid.nt), int(grid.np), float(grid.r1), float(grid.r2), float(grid.t1),
+                    float(grid.t2), float(grid.p1), float(grid.p2), int(bool(grid.periodic)))
+
+
+def sph_field_size(grid, f: int) -> int:
+    g = _grid_struct(grid)
+    return int(load().sph_field_size(C.byref(g), f))
+
+
+def _check(code, what):
+    if code != 0:
+        raise SphError(code, what)
+
+
+class _Ptrs:
+    """double*[5] view of 5 torch tensors or numpy arrays (kept alive)."""
+
+    def __init__(self, fields, shapes, device):
+        import torch
+        if len(fields) != 5:
+            raise ValueError("need 5 fields: p, u_r, u_theta, u_phi, T")
+        self.keep = []
+        ptrs = []
+        for f, shp in zip(fields, shapes):
+            if device:
+                if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == torch.float64):
+                    raise TypeError("device fields must be CUDA float64 tensors")
+                if tuple(f.shape) != tuple(shp) and f.numel() != int(np.prod(shp)):
+                    raise ValueError(f"field shape {tuple(f.shape)} != {tuple(shp)}")
+                f = f.contiguous()
+                self.keep.append(f)
+                ptrs.append(C.cast(C.c_void_p(f.data_ptr()), _DP))
+            else:
+                a = np.ascontiguousarray(f, dtype=np.float64)
+                if a.size != int(np.prod(shp)):
+                    raise ValueError(f"field size {a.size} != {int(np.prod(shp))}")
+                self.keep.append(a)
+                ptrs.append(a.ctypes.data_as(_DP))
+        self.arr = (_DP * 5)(*ptrs)
+
+
+class Solver:
+    """One sector (or shell) and its state on the current CUDA device.
+
+    grid: object with nr, nt, np, r1, r2, t1, t2, p1, p2, periodic.
+    par:  object with gamma, cv, Pr, mu, pinf, g, omega.
+    """
+
+    def __init__(self, grid, par, precision: int = SPH_PREC_FP64, stream=None):
+        import torch
+        L = load()
+        self.grid = grid
+        self._g = _grid_struct(grid)
+        self._p = sph_params(float(par.gamma), float(par.cv), float(par.Pr), float(par.mu), float(par.pinf),
+                             float(par.g), float(par.omega), int(precision))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _CTX()
+        _check(L.sph_create(C.byref(self._g), C.byref(self._p), C.c_void_p(stream.cuda_stream), C.byref(h)),
+               "sph_create")
+        self._h = h
+        self.shapes = grid.shapes()
+
+    # -------------------------------------------------------------- state
+    def set_background(self, p_ref=None, T_ref=None):
+        n = self.grid.nr + 2
+        a = None if p_ref is None else np.ascontiguousarray(p_ref, dtype=np.float64)
+        b = None if T_ref is None else np.ascontiguousarray(T_ref, dtype=np.float64)
+        for v in (a, b):
+            if v is not None and v.size != n:
+                raise ValueError(f"background needs {n} values")
+        _check(load().sph_set_background(self._h, a.ctypes.data_as(_DP) if a is not None else None,
+                                         b.ctypes.data_as(_DP) if b is not None else None), "sph_set_background")
+
+    def set_state(self, fields):
+        dev = not isinstance(fields[0], np.ndarray)
+        p = _Ptrs(fields, self.shapes, dev)
+        _check(load().sph_set_state(self._h, p.arr, int(dev)), "sph_set_state")
+
+    def set_iterate(self, fields):
+        dev = not isinstance(fields[0], np.ndarray)
+        p = _Ptrs(fields, self.shapes, dev)
+        _check(load().sph_set_iterate(self._h, p.arr, int(dev)), "sph_set_iterate")
+
+    def empty(self):
+        import torch
+        return [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes]
+
+    def get_state(self, device: bool = True):
+        if device:
+            out = self.empty()
+            p = _Ptrs(out, self.shapes, True)
+            _check(load().sph_get_state(self._h, p.arr, 1), "sph_get_state")
+            return out
+        out = [np.empty(s) for s in self.shapes]
+        p = _Ptrs(out, self.shapes, False)
+        _check(load().sph_get_state(self._h, p.arr, 0), "sph_get_state")
+        return out
+
+    # --------------------------------------------------------------- step
+    def step(self, dt: float, n_iter: int, source=None, residual: bool = False):
+        src = None
+        on_dev = 0
+        if source is not None:
+            on_dev = int(not isinstance(source[0], np.ndarray))
+            src = _Ptrs(source, self.shapes, bool(on_dev))
+        res = np.zeros(5) if residual else None
+        _check(load().sph_step(self._h, float(dt), int(n_iter), src.arr if src else None, on_dev,
+                               res.ctypes.data_as(_DP) if res is not None else None), "sph_step")
+        return res
+
+    # ------------------------------------------------------------- stages
+    def rhs(self, dt: float, source=None):
+        out = self.empty()
+        po = _Ptrs(out, self.shapes, True)
+        src = None
+        on_dev = 0
+        if source is not None:
+            on_dev = int(not isinstance(source[0], np.ndarray))
+            src = _Ptrs(source, self.shapes, bool(on_dev))
+        _check(load().sph_rhs(self._h, float(dt), src.arr if src else None, on_dev, po.arr), "sph_rhs")
+        return out
+
+    def sweep(self, direction: int, dt: float, rhs_fields):
+        out = self.empty()
+        pi = _Ptrs(rhs_fields, self.shapes, True)
+        po = _Ptrs(out, self.shapes, True)
+        _check(load().sph_sweep(self._h, int(direction), float(dt), pi.arr, po.arr), "sph_sweep")
+        return out
+
+    KERNELS = ("avg", "coef", "rhs", "sweep_r", "sweep_theta", "sweep_phi")
+
+    def profile(self, enable: bool = True):
+        """Start (clear) or stop per-kernel CUDA-event timing inside the library."""
+        _check(load().sph_profile(self._h, int(bool(enable))), "sph_profile")
+
+    def profile_read(self):
+        """{kernel: (total ms, launches)} recorded since profile(True) (synchronises)."""
+        ms = (C.c_double * 8)()
+        cnt = (C.c_longlong * 8)()
+        _check(load().sph_profile_read(self._h, ms, cnt), "sph_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.KERNELS)}
+
+    @property
+    def launches(self) -> int:
+        return int(load().sph_launch_count(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (FP64 mode):
+* each line solve (eqs. spl1-spl3): 1e-12 relative, max norm per field;
+* the right-hand side of eq. (spl1): the oracle forms it in the paper's order
+  (D(U^k-U^n), D U^n, D_M U^k, D_M U^n, each applied separately) and the
+  library in the midpoint form -(U^k-U^n) - tau N(Ubar); both are exact up to
+  rounding, and the rounding is amplified where large flux terms cancel (a
+  nearly solenoidal velocity under gamma p div u).  The bound is therefore the
+  oracle's own disagreement between the two orders: |R - R_paper| <=
+  2 max|R_mid - R_paper| + 1e-12 max|R_paper| per field, R_mid being the oracle's
+  midpoint-form evaluation;
+* whole steps: 1e-10 relative per field.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2004_13887_gb300 as sph
+from inputs import Grid, Params, cases
+from tests.gpu_helpers import cut, cut_bg, perturbed, rel_err, solver_for, subgrid, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    sph.build()
+    oracle.build()
+
+
+def _sector(n=(9, 10, 11)):
+    c = cases.sector_mms(n)
+    it = perturbed(c.exact(c.dt), [1e-2, 1e-4, 1e-2, 1e-3, 1e-2], 3, c.grid)
+    return c.grid, c.par, c.bg, c.init, it, c.source(0.5 * c.dt), c.dt
+
+
+def _bubble(n=(10, 12, 14)):
+    c = cases.bubble(n, seed=2, dt=1.0)
+    it = perturbed(c.init, [5.0, 1e-2, 1e-2, 1e-2, 1e-2], 4, c.grid)
+    return c.grid, c.par, c.bg, c.init, it, None, c.dt
+
+
+def _shell(n=(6, 8, 12), pole=True):
+    t1, t2 = (0.0, math.pi) if pole else (0.3, 2.8)
+    g = Grid(n[0], n[1], n[2], 1.0, 1.3, t1, t2, 0.0, 2 * math.pi, periodic=True)
+    par = Params(gamma=1.4, cv=2.5, Pr=0.7, mu=0.05, pinf=2.0, g=0.3, omega=0.4)
+    rng = np.random.default_rng(8)
+    U = perturbed(g.zeros(), [0.1, 0.05, 0.05, 0.05, 0.1], 5, g)
+    U[2][:, 0] = U[2][:, -1] = 0
+    bg = (np.full(g.nr + 2, 20.0), np.full(g.nr + 2, 30.0))
+    it = perturbed(U, [1e-2] * 5, 6, g)
+    it[2][:, 0] = it[2][:, -1] = 0
+    S = [0.01 * rng.standard_normal(s) for s in g.shapes()]
+    return g, par, bg, U, it, S, 0.01
+
+
+CASES = {"sector": _sector, "bubble": _bubble, "shell_pole": _shell, "shell": lambda: _shell(pole=False),
+         "tiny": lambda: _sector((2, 2, 2)), "ragged": lambda: _sector((3, 7, 5))}
+
+
+def rhs_midpoint(g, par, bg, Un, Uk, dt, S=None):
+    """the oracle's R in midpoint form: -(U^k-U^n) - dt [sum of the four split operators at Ubar + G - S]"""
+    Ub = [0.5 * (a + b) for a, b in zip(Un, Uk)]
+    tot = [np.zeros(s) for s in g.shapes()]
+    for which in range(4):
+        out = oracle.apply_op(g, par, Ub, which, Ub, bg=bg, v_bg=bg)
+        for q in range(5):
+            tot[q] += out[q]
+    R = []
+    for q in range(5):
+        v = -(Uk[q] - Un[q]) - dt * (tot[q] + (par.g if q == 1 else 0.0) - (S[q] if S is not None else 0.0))
+        R.append(v)
+    R[1][0] = R[1][-1] = 0.0
+    R[2][:, 0] = R[2][:, -1] = 0.0
+    if not g.periodic:
+        R[3][:, :, 0] = R[3][:, :, -1] = 0.0
+    return R
+
+
+def rhs_bound(ref, mid):
+    """per field: 2 x the oracle's order-noise + 1e-12 max|R|"""
+    return [2.0 * float(np.max(np.abs(m - r))) + 1e-12 * float(np.max(np.abs(r))) for r, m in zip(ref, mid)]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_parity(name):
+    g, par, bg, Un, Uk, S, dt = CASES[name]()
+    s = solver_for(g, par, bg, Un)
+    s.set_iterate(Uk)
+    R = to_host(s.rhs(dt, S))
+    ref = oracle.rhs(g, par, Un, Uk, dt, bg=bg, S=S)
+    mid = rhs_midpoint(g, par, bg, Un, Uk, dt, S)
+    tol = rhs_bound(ref, mid)
+    for q in range(5):
+        err = float(np.max(np.abs(R[q] - ref[q])))
+        assert err <= tol[q], (name, q, err, tol[q])
+        assert rel_err(R[q], ref[q]) <= 1e-10, (name, q)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_sweep_parity(name, d):
+    g, par, bg, Un, Uk, S, dt = CASES[name]()
+    s = solver_for(g, par, bg, Un)
+    s.set_iterate(Uk)
+    rng = np.random.default_rng(10 + d)
+    rhs = perturbed(g.zeros(), [1.0] * 5, 20 + d, g)
+    x = to_host(s.sweep(d, dt, to_dev(rhs)))
+    ref = oracle.sweep(g, par, Un, Uk, dt, d, rhs, bg=bg)
+    for q in range(5):
+        assert rel_err(x[q], ref[q]) <= 1e-12, (name, d, q, rel_err(x[q], ref[q]))
+
+
+def _steps(g, par, bg, U0, dt, K, nsteps, source=None):
+    s = solver_for(g, par, bg, U0)
+    Uo = U0
+    for n in range(nsteps):
+        S = source((n + 0.5) * dt) if source else None
+        s.step(dt, K, S)
+        Uo, _ = oracle.step(g, par, Uo, dt, K, bg=bg, S=S)
+    return to_host(s.get_state()), Uo, s
+
+
+def test_step_parity_sector_config():
+    """Regional sector 32^3, manufactured solution, Mach 1e-2, dt = 1e-3, 10 steps, K = 2."""
+    c = cases.sector_mms((32, 32, 32))
+    U, Uo, s = _steps(c.grid, c.par, c.bg, c.init, c.dt, 2, 10, c.source)
+    for q in range(5):
+        assert rel_err(U[q], Uo[q]) <= 1e-10, (q, rel_err(U[q], Uo[q]))
+    # and the scheme still tracks the manufactured solution
+    ex = c.exact(10 * c.dt)
+    assert rel_err(U[0], ex[0]) < 1e-2
+
+
+@pytest.mark.parametrize("name", ["bubble", "shell_pole", "ragged", "tiny"])
+def test_step_parity(name):
+    g, par, bg, Un, _, S, dt = CASES[name]()
+    U, Uo, s = _steps(g, par, bg, Un, dt, 3, 3, (lambda t: S) if S is not None else None)
+    for q in range(5):
+        assert rel_err(U[q], Uo[q]) <= 1e-10, (name, q, rel_err(U[q], Uo[q]))
+
+
+def test_residual_and_iteration_convergence():
+    c = cases.sector_mms((10, 12, 14))
+    s = solver_for(c.grid, c.par, c.bg, c.init)
+    res = [s.step(c.dt, K, c.source(0.5 * c.dt), residual=True) for K in (1,)]
+    s.set_state(c.init)
+    r2 = s.step(c.dt, 2, c.source(0.5 * c.dt), residual=True)
+    s.set_state(c.init)
+    r6 = s.step(c.dt, 6, c.source(0.5 * c.dt), residual=True)
+    _, ro = oracle.step(c.grid, c.par, c.init, c.dt, 2, bg=c.bg, S=c.source(0.5 * c.dt))
+    assert np.allclose(r2, ro, rtol=1e-8)
+    assert np.all(r6 < 1e-3 * r2)
+
+
+def test_nonfinite_state_is_rejected_and_state_kept():
+    c = cases.sector_mms((6, 6, 6))
+    s = solver_for(c.grid, c.par, c.bg, c.init)
+    bad = [f.copy() for f in c.init]
+    bad[0][2, 3, 1] = np.nan
+    s.set_state(bad)
+    with pytest.raises(sph.SphError) as e:
+        s.step(c.dt, 2)
+    assert e.value.code in (-3, -4)
+    after = s.get_state(device=False)
+    assert np.isnan(after[0][2, 3, 1])
+    with pytest.raises(sph.SphError) as e:
+        s.step(-1.0, 2)
+    assert e.value.code == -1
+
+
+# ---------------------------------------------------------------- full size
+
+@pytest.fixture(scope="module")
+def full_bubble():
+    """The benchmark workload: rising thermal bubble on 128 x 256 x 256."""
+    c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
+    it = perturbed(c.init, [2.0, 5e-3, 5e-3, 5e-3, 5e-3], 9, c.grid)
+    s = solver_for(c.grid, c.par, c.bg, c.init)
+    s.set_iterate(it)
+    return c, it, s
+
+
+def test_full_size_rhs_sampled(full_bubble):
+    c, it, s = full_bubble
+    g = c.grid
+    R = to_host(s.rhs(c.dt))
+    rng = np.random.default_rng(12)
+    pts = [(0, 0, 0), (g.nr - 1, g.nt - 1, g.np - 1)] + [tuple(rng.integers(0, n) for n in (g.nr, g.nt, g.np))
+                                                       for _ in range(6)]
+    for (i, j, k) in pts:
+        # the whole radial extent: a sub-range would recompute dr with different
+        # rounding, and the r-momentum row cancels (1/rho) dp/dr against g
+        i0, i1 = 0, g.nr
+        j0, j1 = max(0, j - 3), min(g.nt, j + 4)
+        k0, k1 = max(0, k - 3), min(g.np, k + 4)
+        sg = subgrid(g, i0, i1, j0, j1, k0, k1)
+        un, uk, sbg = cut(g, c.init, i0, i1, j0, j1, k0, k1), cut(g, it, i0, i1, j0, j1, k0, k1), cut_bg(c.bg, i0, i1)
+        ref = oracle.rhs(sg, c.par, un, uk, c.dt, bg=sbg)
+        mid = rhs_midpoint(sg, c.par, sbg, un, uk, c.dt)
+        noise = [float(np.max(np.abs(m - r))) for r, m in zip(ref, mid)]
+        li, lj, lk = i - i0, j - j0, k - k0
+        checks = [(0, R[0][i, j, k], ref[0][li, lj, lk]), (4, R[4][i, j, k], ref[4][li, lj, lk])]
+        if 0 < i:
+            checks.append((1, R[1][i, j, k], ref[1][li, lj, lk]))
+        if 0 < j:
+            checks.append((2, R[2][i, j, k], ref[2][li, lj, lk]))
+        if 0 < k:
+            checks.append((3, R[3][i, j, k], ref[3][li, lj, lk]))
+        for q, a, b in checks:
+            assert abs(a - b) <= 2.0 * noise[q] + 1e-12 * abs(b) + 1e-300, ((i, j, k), q, a, b, noise[q])
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_full_size_lines_sampled(full_bubble, d):
+    c, it, s = full_bubble
+    g = c.grid
+    rhs = perturbed(g.zeros(), [1.0] * 5, 30 + d, g)
+    x = to_host(s.sweep(d, c.dt, to_dev(rhs)))
+    rng = np.random.default_rng(40 + d)
+    for _ in range(3):
+        i, j, k = (int(rng.integers(0, n)) for n in (g.nr, g.nt, g.np))
+        lo = [max(0, v - 3) for v in (i, j, k)]
+        hi = [min(n, v + 4) for v, n in zip((i, j, k), (g.nr, g.nt, g.np))]
+        lo[d], hi[d] = 0, (g.nr, g.nt, g.np)[d]
+        lo[0], hi[0] = 0, g.nr   # whole radial extent (see the rhs test)
+        sg = subgrid(g, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2])
+        box = (lo[0], hi[0], lo[1], hi[1], lo[2], hi[2])
+        ref = oracle.sweep(sg, c.par, cut(g, c.init, *box), cut(g, it, *box), c.dt, d, cut(g, rhs, *box),
+                           bg=cut_bg(c.bg, lo[0], hi[0]))
+        sl_full = [slice(i, i + 1), slice(j, j + 1), slice(k, k + 1)]
+        sl_loc = [slice(i - lo[0], i - lo[0] + 1), slice(j - lo[1], j - lo[1] + 1), slice(k - lo[2], k - lo[2] + 1)]
+        sl_full[d] = slice(None)
+        sl_loc[d] = slice(None)
+        for q in range(5):
+            a = x[q][tuple(sl_full)]
+            b = ref[q][tuple(sl_loc)]
+            if b.size and np.max(np.abs(b)) > 0:
+                assert rel_err(a, b) <= 1e-12, (d, q, (i, j, k), rel_err(a, b))
+
+
+def test_full_size_step_symmetry():
+    """Bubble on the sector axis, no rotation: a full-size step keeps the mirror
+    symmetry in theta and phi (a property the exact scheme has at any size)."""
+    c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
+    s = solver_for(c.grid, c.par, c.bg, c.init)
+    for _ in range(2):
+        s.step(c.dt, 2)
+    p, ur, ut, up, T = to_host(s.get_state())
+    # rounding of the mirrored metric values enters through the ~1e5 Pa background
+    # pressure and the 300 K background temperature: bound p and T relative to
+    # the background, velocities relative to the acoustic speed scale
+    cs = math.sqrt(c.par.gamma * c.bg[0][1] / (c.bg[0][1] / (c.par.cv * (c.par.gamma - 1) * c.bg[1][1])))
+    scales = {"p": np.max(np.abs(c.bg[0])), "T": np.max(np.abs(c.bg[1])), "ur": cs, "ut": cs, "up": cs}
+    for name, f, st, sp in (("p", p, 1, 1), ("ur", ur, 1, 1), ("T", T, 1, 1), ("ut", ut, -1, 1), ("up", up, 1, -1)):
+        a_t = np.max(np.abs(f - st * f[:, ::-1, :])) / scales[name]
+        a_p = np.max(np.abs(f - sp * f[:, :, ::-1])) / scales[name]
+        assert a_t <= 1e-14 and a_p <= 1e-14, (name, a_t, a_p)
+    assert np.max(np.abs(ur)) > 1e-4
