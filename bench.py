@@ -141,7 +141,7 @@ def run_ours(args, rank, world, dist):
     N = g.npoints
     solver = sph.Solver(g, c.par, precision=sph.SPH_PREC_FP64)
     solver.set_background(*c.bg)
-    dev = [torch.from_numpy(f).cuda() for f in c.init]
+    dev = [torch.from_numpy(f.copy()).cuda() for f in c.init]
     solver.set_state(dev)
     stream = solver.stream
 

@@ -21,7 +21,7 @@ import pytest
 import oracle
 import paper_2004_13887_gb300 as sph
 from inputs import Grid, Params, cases
-from tests.gpu_helpers import cut, cut_bg, perturbed, rel_err, solver_for, subgrid, to_dev, to_host
+from tests.gpu_helpers import perturbed, rel_err, solver_for, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -174,10 +174,12 @@ def test_nonfinite_state_is_rejected_and_state_kept():
 
 
 # ---------------------------------------------------------------- full size
+# The benchmark workload itself (rising thermal bubble, 128 x 256 x 256, the
+# launch configuration bench.py times).  The oracle runs on the whole grid: on
+# the GPU host's cores this takes seconds, so every output is compared.
 
 @pytest.fixture(scope="module")
 def full_bubble():
-    """The benchmark workload: rising thermal bubble on 128 x 256 x 256."""
     c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
     it = perturbed(c.init, [2.0, 5e-3, 5e-3, 5e-3, 5e-3], 9, c.grid)
     s = solver_for(c.grid, c.par, c.bg, c.init)
@@ -185,62 +187,32 @@ def full_bubble():
     return c, it, s
 
 
-def test_full_size_rhs_sampled(full_bubble):
+def test_full_size_rhs(full_bubble):
     c, it, s = full_bubble
-    g = c.grid
     R = to_host(s.rhs(c.dt))
-    rng = np.random.default_rng(12)
-    pts = [(0, 0, 0), (g.nr - 1, g.nt - 1, g.np - 1)] + [tuple(rng.integers(0, n) for n in (g.nr, g.nt, g.np))
-                                                       for _ in range(6)]
-    for (i, j, k) in pts:
-        # the whole radial extent: a sub-range would recompute dr with different
-        # rounding, and the r-momentum row cancels (1/rho) dp/dr against g
-        i0, i1 = 0, g.nr
-        j0, j1 = max(0, j - 3), min(g.nt, j + 4)
-        k0, k1 = max(0, k - 3), min(g.np, k + 4)
-        sg = subgrid(g, i0, i1, j0, j1, k0, k1)
-        un, uk, sbg = cut(g, c.init, i0, i1, j0, j1, k0, k1), cut(g, it, i0, i1, j0, j1, k0, k1), cut_bg(c.bg, i0, i1)
-        ref = oracle.rhs(sg, c.par, un, uk, c.dt, bg=sbg)
-        mid = rhs_midpoint(sg, c.par, sbg, un, uk, c.dt)
-        noise = [float(np.max(np.abs(m - r))) for r, m in zip(ref, mid)]
-        li, lj, lk = i - i0, j - j0, k - k0
-        checks = [(0, R[0][i, j, k], ref[0][li, lj, lk]), (4, R[4][i, j, k], ref[4][li, lj, lk])]
-        if 0 < i:
-            checks.append((1, R[1][i, j, k], ref[1][li, lj, lk]))
-        if 0 < j:
-            checks.append((2, R[2][i, j, k], ref[2][li, lj, lk]))
-        if 0 < k:
-            checks.append((3, R[3][i, j, k], ref[3][li, lj, lk]))
-        for q, a, b in checks:
-            assert abs(a - b) <= 2.0 * noise[q] + 1e-12 * abs(b) + 1e-300, ((i, j, k), q, a, b, noise[q])
+    ref = oracle.rhs(c.grid, c.par, c.init, it, c.dt, bg=c.bg)
+    mid = rhs_midpoint(c.grid, c.par, c.bg, c.init, it, c.dt)
+    tol = rhs_bound(ref, mid)
+    for q in range(5):
+        err = float(np.max(np.abs(R[q] - ref[q])))
+        assert err <= tol[q], (q, err, tol[q])
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
-def test_full_size_lines_sampled(full_bubble, d):
+def test_full_size_sweeps(full_bubble, d):
     c, it, s = full_bubble
-    g = c.grid
-    rhs = perturbed(g.zeros(), [1.0] * 5, 30 + d, g)
+    rhs = perturbed(c.grid.zeros(), [1.0] * 5, 30 + d, c.grid)
     x = to_host(s.sweep(d, c.dt, to_dev(rhs)))
-    rng = np.random.default_rng(40 + d)
-    for _ in range(3):
-        i, j, k = (int(rng.integers(0, n)) for n in (g.nr, g.nt, g.np))
-        lo = [max(0, v - 3) for v in (i, j, k)]
-        hi = [min(n, v + 4) for v, n in zip((i, j, k), (g.nr, g.nt, g.np))]
-        lo[d], hi[d] = 0, (g.nr, g.nt, g.np)[d]
-        lo[0], hi[0] = 0, g.nr   # whole radial extent (see the rhs test)
-        sg = subgrid(g, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2])
-        box = (lo[0], hi[0], lo[1], hi[1], lo[2], hi[2])
-        ref = oracle.sweep(sg, c.par, cut(g, c.init, *box), cut(g, it, *box), c.dt, d, cut(g, rhs, *box),
-                           bg=cut_bg(c.bg, lo[0], hi[0]))
-        sl_full = [slice(i, i + 1), slice(j, j + 1), slice(k, k + 1)]
-        sl_loc = [slice(i - lo[0], i - lo[0] + 1), slice(j - lo[1], j - lo[1] + 1), slice(k - lo[2], k - lo[2] + 1)]
-        sl_full[d] = slice(None)
-        sl_loc[d] = slice(None)
-        for q in range(5):
-            a = x[q][tuple(sl_full)]
-            b = ref[q][tuple(sl_loc)]
-            if b.size and np.max(np.abs(b)) > 0:
-                assert rel_err(a, b) <= 1e-12, (d, q, (i, j, k), rel_err(a, b))
+    ref = oracle.sweep(c.grid, c.par, c.init, it, c.dt, d, rhs, bg=c.bg)
+    for q in range(5):
+        assert rel_err(x[q], ref[q]) <= 1e-12, (d, q, rel_err(x[q], ref[q]))
+
+
+def test_full_size_step():
+    c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
+    U, Uo, s = _steps(c.grid, c.par, c.bg, c.init, c.dt, 2, 2)
+    for q in range(5):
+        assert rel_err(U[q], Uo[q]) <= 1e-10, (q, rel_err(U[q], Uo[q]))
 
 
 def test_full_size_step_symmetry():
