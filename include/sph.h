@@ -127,6 +127,28 @@ int sph_profile_read(sph_ctx* ctx, double* ms, long long* count);
 void sph_destroy(sph_ctx* ctx);
 const char* sph_strerror(int code);
 
+/* Batched 3x3-block tridiagonal solve that allocates no device memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc (a host that forbids allocation after start-up, a plug-in
+ * that only receives device pointers, a capture-time memory budget).  It runs
+ * the block Thomas elimination of the line sweeps (no pivoting between blocks)
+ * on systems the caller assembled:
+ *     A_m x_{m-1} + B_m x_m + C_m x_{m+1} = d_m,  m = 0..n-1  (A_0, C_{n-1} unused)
+ * for nlines independent lines.  All pointers are device pointers of the current
+ * device; blocks are 3x3 row-major, block (l, m) at offset (l*n + m)*9 of A, B,
+ * C, and vectors at (l*n + m)*3 of d and x (x may not alias the inputs).
+ * Scratch: a file-scope device array of SPH_NOALLOC_MAX_BLOCKS * 12 doubles
+ * (12.6 MB) that every GPU loading the library holds until exit; nlines*n above
+ * SPH_NOALLOC_MAX_BLOCKS returns SPH_ERR_ARG.  The first call on a device looks
+ * up the array's device address, so make it before any stream capture.  The
+ * work is queued on `stream` (NULL = legacy default) and the call returns
+ * without synchronising; a zero pivot fills that line's x with NaN.  Every call
+ * shares the one array, so calls that overlap on the GPU (other streams, other
+ * host threads) race: serialise them. */
+#define SPH_NOALLOC_MAX_BLOCKS 131072
+int sph_block_thomas_noalloc(int nlines, int n, const double* A, const double* B, const double* C,
+                             const double* d, double* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ SIGNATURES = {
     "sph_profile": ([_CTX, C.c_int], C.c_int),
     "sph_profile_read": ([_CTX, _DP, C.POINTER(C.c_longlong)], C.c_int),
     "sph_destroy": ([_CTX], None),
+    "sph_block_thomas_noalloc": ([C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP, C.c_void_p], C.c_int),
     "sph_strerror": ([C.c_int], C.c_char_p),
 }
 
@@ -94,6 +95,29 @@ def sph_field_size(grid, f: int) -> int:
 def _check(code, what):
     if code != 0:
         raise SphError(code, what)
+
+
+NOALLOC_MAX_BLOCKS = 131072
+
+
+def block_thomas_noalloc(A, B, Cb, d, stream=None):
+    """Solve nlines independent 3x3-block tridiagonal lines without any device
+    allocation inside the library (sph_block_thomas_noalloc).
+
+    A, B, Cb: CUDA float64 tensors (nlines, n, 3, 3); d: (nlines, n, 3).  The
+    output tensor is allocated here by torch, by the caller's side."""
+    import torch
+    nlines, n = int(B.shape[0]), int(B.shape[1])
+    for t in (A, B, Cb, d):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError("A, B, C, d must be contiguous CUDA float64 tensors")
+    x = torch.empty((nlines, n, 3), dtype=torch.float64, device=B.device)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    p = [C.cast(C.c_void_p(t.data_ptr()), _DP) for t in (A, B, Cb, d, x)]
+    _check(load().sph_block_thomas_noalloc(nlines, n, *p, C.c_void_p(stream.cuda_stream)),
+           "sph_block_thomas_noalloc")
+    return x
 
 
 class _Ptrs:

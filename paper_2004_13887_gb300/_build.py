@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsph.so")
-SOURCES = ["sph.cu"]
+SOURCES = ["sph.cu", "sph_noalloc.cu"]
 HEADERS = ["sph_device.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
