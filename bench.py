@@ -38,8 +38,19 @@ UNIT = "points/s"
 
 # FP64 operations (DADD + DMUL + 2 DFMA, counted from the kernel's SASS
 # instruction mix with ncu) per line point of each kernel; None = not measured.
-FP64_FLOP_PER_POINT = {"rhs": None, "coef": None, "sweep_r": None, "sweep_theta": None, "sweep_phi": None}
-FP64_PEAK_TFLOPS = 1.26   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25)
+FP64_FLOP_PER_POINT = {"rhs": 1103.2, "coef": 121.4, "sweep": 471.6}
+FP64_PEAK_TFLOPS = 1.257  # measured FP64 FMA throughput on the machine's GB300 (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)
+HBM_PEAK_GBS = 6780.4     # measured copy bandwidth of the GB300s
+
+# Algorithmic bytes per grid point of each mixed-precision kernel launch: the
+# information it must move once -- no coefficient planes, no elimination
+# scratch, no halo re-reads (those are what ncu's DRAM traffic adds on top):
+#   sweep_r/theta : rhs in (5 x 4 B) + Ubar in (5 x 4) + increment out (5 x 4)        =  60
+#   sweep_phi     : rhs in (5 x 4) + Ubar in (5 x 4) + U^k in and out (2 x 5 x 8)     = 120
+#   rhs           : U^n and U^k in (2 x 5 x 8) + R out (5 x 4)                         = 100
+#   coef          : Ubar in (5 x 4) + 14 coefficient planes out (14 x 4)               =  76
+#   avg           : U^n and U^k in (2 x 5 x 8) + Ubar out (5 x 4)                      = 100
+MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rhs": 100, "coef": 76, "avg": 100}
 
 
 def log(*a):
@@ -124,6 +135,60 @@ def oracle_sample(steps: int):
 
 # ------------------------------------------------------------- our arm
 
+def time_path(solver, args, dist, local):
+    """warm-up, then the timed steps (CUDA events on the library's stream)"""
+    import torch
+    for _ in range(args.warmup):
+        solver.step(DT, K_ITER)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    l0 = solver.launches
+    solver.profile(True)
+    e0.record(solver.stream)
+    for _ in range(args.steps):
+        solver.step(DT, K_ITER)
+    e1.record(solver.stream)
+    torch.cuda.synchronize()
+    kern = solver.profile_read()
+    solver.profile(False)
+    launches = solver.launches - l0
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, kern, launches, clocks
+
+
+def field_errors(Um, Ud, c):
+    """relative L2 error of the mixed state against FP64, per physical field"""
+    import numpy as np
+    bgp, bgT = c.bg
+    par = c.par
+    Rg = par.cv * (par.gamma - 1.0)
+    out = {}
+    P = [U[0] + bgp[1:-1][:, None, None] for U in (Um, Ud)]
+    T = [U[4] + bgT[1:-1][:, None, None] for U in (Um, Ud)]
+    rho = [(p + par.pinf) / (Rg * t) for p, t in zip(P, T)]
+    th = [t * (bgp[1] / p) ** (Rg / (par.gamma * par.cv)) for p, t in zip(P, T)]
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    out["p"], out["rho"], out["theta"], out["T"] = rel(*P), rel(*rho), rel(*th), rel(*T)
+    num = sum(float(np.linalg.norm(Um[q] - Ud[q])) ** 2 for q in (1, 2, 3))
+    den = sum(float(np.linalg.norm(Ud[q])) ** 2 for q in (1, 2, 3))
+    out["u"] = math.sqrt(num / max(den, 1e-300))
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import numpy as np
     import torch
@@ -139,56 +204,51 @@ def run_ours(args, rank, world, dist):
     c = cases.bubble(GRID, seed=1, dt=DT)
     g = c.grid
     N = g.npoints
-    solver = sph.Solver(g, c.par, precision=sph.SPH_PREC_FP64)
-    solver.set_background(*c.bg)
     dev = [torch.from_numpy(f.copy()).cuda() for f in c.init]
+
+    # FP64 path, timed first (the reference point of the mixed path's error)
+    U64 = None
+    if args.only in ("both", "fp64"):
+        s64 = sph.Solver(g, c.par, precision=sph.SPH_PREC_FP64)
+        s64.set_background(*c.bg)
+        s64.set_state(dev)
+        t64, kern64, _, _ = time_path(s64, args, dist, local)
+        U64 = [f.cpu().numpy() for f in s64.get_state()]
+        s64.close()
+        del s64
+        torch.cuda.empty_cache()
+    if args.only == "fp64":
+        return {"metric": METRIC, "value": N * args.steps * world / (t64 / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64"}}
+
+    solver = sph.Solver(g, c.par, precision=sph.SPH_PREC_MIXED)
+    solver.set_background(*c.bg)
     solver.set_state(dev)
     stream = solver.stream
 
-    for _ in range(args.warmup):
-        solver.step(DT, K_ITER)
-    torch.cuda.synchronize()
-
-    sampler = ClockSampler(local)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    l0 = solver.launches
-    solver.profile(True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        solver.step(DT, K_ITER)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    kern = solver.profile_read()
-    solver.profile(False)
-    launches = solver.launches - l0
-    clocks = sampler.stop()
-    if dist is not None:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max, kern, launches, clocks = time_path(solver, args, dist, local)
     value = N * args.steps * world / (t_max / 1e3)
+    Um = [f.cpu().numpy() for f in solver.get_state()]
+    errors, fp64 = None, None
+    if U64 is not None:
+        errors = {"metric": "relative L2 after warmup+steps steps", **field_errors(Um, U64, c)}
+        fp64 = {"value": N * args.steps * world / (t64 / 1e3), "ms_per_step": t64 / args.steps,
+                "kernel_shares": {k: round(v[0] / max(sum(x[0] for x in kern64.values()), 1e-30), 4)
+                                  for k, v in kern64.items() if v[1]}}
 
-    # dominant kernel and its roofline
+    # dominant kernel of the mixed step and its HBM roofline
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_n = kern[dom]
     per_launch_ms = dom_ms / max(dom_n, 1)
-    units = N   # every kernel processes each cell once per launch
-    fpp = FP64_FLOP_PER_POINT.get(dom)
-    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS,
-            "peak_source": "FP64 nominal from unit counts and clocks (no measured FP64 peak on file)",
-            "launch_ms": per_launch_ms, "traffic": None}
-    if fpp:
-        achieved = fpp * units / (per_launch_ms * 1e-3) / 1e12
-        roof.update(achieved=achieved, frac=achieved / FP64_PEAK_TFLOPS, flop_per_point=fpp)
+    bpp = MIXED_BYTES_PER_POINT.get(dom)
+    roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "peak": HBM_PEAK_GBS,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "launch_ms": per_launch_ms, "traffic": None, "bytes_per_point": bpp}
+    if bpp:
+        achieved = bpp * N / (per_launch_ms * 1e-3) / 1e9
+        roof.update(achieved=achieved, frac=achieved / HBM_PEAK_GBS)
     else:
         roof.update(achieved=None, frac=None)
     shares = {k: round(v[0] / max(sum(x[0] for x in kern.values()), 1e-30), 4) for k, v in kern.items() if v[1]}
@@ -216,12 +276,15 @@ def run_ours(args, rank, world, dist):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(GRID), "K": K_ITER, "dt_s": DT, "precision": "fp64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "K": K_ITER, "dt_s": DT,
+                   "precision": "mixed: FP32 stencils and line solves; FP64 state, update, div u, cyclic corrections",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "no flush: the state (5 FP64 fields, 336 MB) and per-iteration buffers exceed the 129 MB L2"},
         "roofline": roof,
         "kernel_shares": shares,
+        "error_vs_fp64": errors,
+        "fp64_plain": fp64,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
                 "steps": e2e_steps},
         "gpu_launches": launches,
@@ -269,6 +332,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default=None, help="nr,nt,np of a smaller sector (profiling of small cases)")
+    ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both",
+                    help="profiling: run one path only (the JSON line then lacks the other)")
     args = ap.parse_args()
     if args.grid:
         global GRID, WORKLOAD

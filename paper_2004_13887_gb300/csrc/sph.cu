@@ -5,9 +5,9 @@
 // operators of Appendix B.
 //
 // One iteration k -> k+1 is five launches:
-//   avg   : Ubar = (U^n + U^{n+1,k})/2                      (skipped at k = 0)
-//   coef  : per-centre coefficients frozen at Ubar (p+pi_inf, T, rho, beta,
-//           centre velocities, grad u with metric terms)
+//   avg   : Ubar = (U^n + U^{n+1,k})/2 in the bulk type
+//   coef  : per-centre coefficients frozen at Ubar (p+pi_inf, T, rho, rho-rho_ref,
+//           beta, centre velocities, grad u with metric terms)
 //   rhs   : R = -(U^k - U^n) - tau [N(Ubar) + G - S]  (the right-hand side of
 //           eq. spl1 after the linearity of D(Ubar) is used: the D(U^k - U^n),
 //           D U^n and D_M terms collapse to the full operator at Ubar)
@@ -16,6 +16,13 @@
 //           Thomas for the two transverse velocities; cyclic lines (periodic phi)
 //           by a rank-3 Woodbury / Sherman-Morrison correction.  The phi sweep
 //           also applies U^{k+1} = U^k + x and accumulates the increment norm.
+//
+// Precision: everything is templated on the bulk type R.  R = double is the
+// plain FP64 scheme.  R = float ("mixed") keeps U^n, U^{n+1,k}, their update and
+// the -(U^k - U^n) part of R in FP64, forms div(Ubar) -- which multiplies
+// gamma (p + pi_inf) and nearly cancels at low Mach number -- in FP64 from the
+// FP64 state, writes the hydrostatic part of the r-momentum row through density
+// perturbations, and combines the cyclic corrections in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -33,197 +40,244 @@ using namespace sph;
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void k_avg(long n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o) {
+template <typename R>
+__global__ void k_avg(long n, const double* __restrict__ a, const double* __restrict__ b, R* __restrict__ o) {
   long s = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = 0.5 * (a[t] + b[t]);
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = (R)(0.5 * (a[t] + b[t]));
 }
 
-__global__ void k_coef(Geo g, Par P, CF ub, Coef c) {
+template <typename R>
+__global__ void k_cvt(long n, const R* __restrict__ a, double* __restrict__ o) {
+  long s = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = (double)a[t];
+}
+
+template <typename R>
+__global__ void k_cvt_in(long n, const double* __restrict__ a, R* __restrict__ o) {
+  long s = (long)gridDim.x * blockDim.x;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = (R)a[t];
+}
+
+template <typename R>
+__global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long N = (long)g.nr * g.nt * g.np;
   if (t >= N) return;
   int k = (int)(t % g.np), j = (int)((t / g.np) % g.nt), i = (int)(t / ((long)g.np * g.nt));
-  const double *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
-  double pb = cval(g, ub.f[0], g.bgp, i, j, k) + P.pinf;
-  double tb = cval(g, ub.f[4], g.bgT, i, j, k);
-  double ipb = 1.0 / pb, itb = 1.0 / tb;
-  c.Pb[t] = pb;
-  c.Tb[t] = tb;
-  c.rho[t] = pb * itb / P.Rg;
-  c.beta[t] = (P.gamma - 1.0) * tb * ipb;
-  double ur = hr(g, UR, i, j, k), ut = ht(g, UT, i, j, k), up = hp(g, UP, i, j, k);
+  const R *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
+  // thermodynamics in FP64 from background + perturbation
+  double pref = g.bgp[i + 1] + P.pinf, Tref = g.bgT[i + 1];
+  double pp = (double)ub.f[0][t], Tp = (double)ub.f[4][t];
+  double pb = pref + pp, tb = Tref + Tp;
+  c.Pb[t] = (R)pb;
+  c.Tb[t] = (R)tb;
+  c.rho[t] = (R)(pb / (P.Rg * tb));
+  c.drho[t] = (R)((pp * Tref - pref * Tp) / (P.Rg * Tref * tb));
+  c.beta[t] = (R)((P.gamma - 1.0) * tb / pb);
+  R ur = hr(g, UR, i, j, k), ut = ht(g, UT, i, j, k), up = hp(g, UP, i, j, k);
   c.uc0[t] = ur; c.uc1[t] = ut; c.uc2[t] = up;
-  double ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
+  R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j], h = R(0.5);
   c.grr[t] = (vr(g, UR, i + 1, j, k) - vr(g, UR, i, j, k)) * g.idr;
   c.gtt[t] = (vt(g, UT, i, j + 1, k) - vt(g, UT, i, j, k)) * ir * g.idth + ur * ir;
   c.gpp[t] = (vp(g, UP, i, j, k + 1) - vp(g, UP, i, j, k)) * ir * is * g.idph + ur * ir + ut * cot * ir;
-  double grt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * 0.5 * g.idr;
-  double gtr = (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * 0.5 * ir * g.idth - ut * ir;
-  double grp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * 0.5 * g.idr;
-  double gpr = (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * 0.5 * ir * is * g.idph - up * ir;
-  double gtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * 0.5 * ir * g.idth;
-  double gpt = (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * 0.5 * ir * is * g.idph - up * cot * ir;
+  R grt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr;
+  R gtr = (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth - ut * ir;
+  R grp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr;
+  R gpr = (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * h * ir * is * g.idph - up * ir;
+  R gtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * h * ir * g.idth;
+  R gpt = (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * h * ir * is * g.idph - up * cot * ir;
   c.srt[t] = grt + gtr;
   c.srp[t] = grp + gpr;
   c.stp[t] = gtp + gpt;
 }
 
+// div(Ubar) at centre (i,j,k), in FP64 from U^n and U^k (Ubar = (U^n+U^k)/2).
+__device__ __forceinline__ double div_ubar(const Geo<double>& g, const CF<double>& un, const CF<double>& uk, int i,
+                                           int j, int k) {
+  const double *ur0 = un.f[1], *ur1 = uk.f[1], *ut0 = un.f[2], *ut1 = uk.f[2], *up0 = un.f[3], *up1 = uk.f[3];
+  long a0 = IRf(g, i, j, k), a1 = IRf(g, i + 1, j, k);
+  long b0 = ITf(g, i, j, k), b1 = ITf(g, i, j + 1, k);
+  int kp = g.per ? wrapk(g, k + 1) : k + 1;
+  long c0 = IPf(g, i, j, k), c1 = IPf(g, i, j, kp);
+  double ir = g.irc[i], is = g.isc[j];
+  double f0 = g.rf[i] * g.rf[i], f1 = g.rf[i + 1] * g.rf[i + 1];
+  double dr_ = (f1 * (ur0[a1] + ur1[a1]) - f0 * (ur0[a0] + ur1[a0])) * ir * ir * g.idr;
+  double dt_ = (g.sf[j + 1] * (ut0[b1] + ut1[b1]) - g.sf[j] * (ut0[b0] + ut1[b0])) * ir * is * g.idth;
+  double dp_ = ((up0[c1] + up1[c1]) - (up0[c0] + up1[c0])) * ir * is * g.idph;
+  return 0.5 * (dr_ + dt_ + dp_);
+}
+
 // N(Ubar) rows and R = -(U^k - U^n) - tau (N + G - S); one thread per centre
 // also owns the lower r-, theta- and phi-faces of its cell.
-__global__ void k_rhs(Geo g, Par P, Coef c, CF ub, CF un, CF uk, CF src, int has_src, double tau, MF R) {
+template <typename R>
+__global__ void k_rhs(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<double> un, CF<double> uk,
+                      CF<double> src, int has_src, double tau, MF<R> Rout) {
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   long N = (long)g.nr * g.nt * g.np;
   if (t >= N) return;
   int k = (int)(t % g.np), j = (int)((t / g.np) % g.nt), i = (int)(t / ((long)g.np * g.nt));
-  const double *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
-  double mu = P.mu, gm = P.gamma, om = P.omega;
-  double ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
+  const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
+  R mu = (R)P.mu, gm = (R)P.gamma, om = (R)P.omega, h = R(0.5);
+  R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
 
   // ---- p- and T-rows at the centre
   {
-    double accp = 0.0, accT = 0.0;
+    R accp = R(0), accT = R(0);
+    R ap = R(0), aT = R(0);
     for (int d = 0; d < 3; d++) {
       int di = d == 0, dj = d == 1, dk = d == 2;
-      double pv[3], Tv[3], uv[2];
+      R pv[3], Tv[3], uv[2];
       for (int s = -1; s <= 1; s++) {
-        pv[s + 1] = cval(g, Pp, g.bgp, i + s * di, j + s * dj, k + s * dk);
-        Tv[s + 1] = cval(g, TT, g.bgT, i + s * di, j + s * dj, k + s * dk);
+        pv[s + 1] = cpert(g, Pp, i + s * di, j + s * dj, k + s * dk);
+        Tv[s + 1] = cpert(g, TT, i + s * di, j + s * dj, k + s * dk);
       }
       if (d == 0) { uv[0] = UR[IRf(g, i, j, k)]; uv[1] = UR[IRf(g, i + 1, j, k)]; }
       else if (d == 1) { uv[0] = UT[ITf(g, i, j, k)]; uv[1] = UT[ITf(g, i, j + 1, k)]; }
       else { uv[0] = vp(g, UP, i, j, k); uv[1] = vp(g, UP, i, j, k + 1); }
-      double wp[3], wT[3], wu[2];
-      row_c(g, P, c, d, 0, i, j, k, wp, wT, wu);
-      accp += wp[0] * pv[0] + wp[1] * pv[1] + wp[2] * pv[2] + wT[0] * Tv[0] + wT[1] * Tv[1] + wT[2] * Tv[2]
-            + wu[0] * uv[0] + wu[1] * uv[1];
-      row_c(g, P, c, d, 1, i, j, k, wp, wT, wu);
-      accT += wT[0] * Tv[0] + wT[1] * Tv[1] + wT[2] * Tv[2] + wu[0] * uv[0] + wu[1] * uv[1];
+      RowC<R> w;
+      row_c(g, P, c, d, 0, i, j, k, w);
+      accp += w.wp[0] * pv[0] + w.wp[2] * pv[2] + w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2]
+            + w.wv[0] * uv[0] + w.wv[1] * uv[1];
+      if (d == 0) accp += w.adv * g.dbgp[i] - w.dif * g.lapT[i];
+      ap = w.a;
+      row_c(g, P, c, d, 1, i, j, k, w);
+      accT += w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2] + w.wv[0] * uv[0] + w.wv[1] * uv[1];
+      if (d == 0) accT += w.adv * g.dbgT[i] - w.dif * g.lapT[i];
+      aT = w.a;
     }
-    double xrt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * 0.5 * g.idr
-               + (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * 0.5 * ir * g.idth;
-    double xrp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * 0.5 * g.idr
-               + (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * 0.5 * ir * is * g.idph;
-    double xtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * 0.5 * ir * g.idth
-               + (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * 0.5 * ir * is * g.idph;
-    double cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
-    accp += -mu * (gm - 1.0) * cross;
+    double divu = div_ubar(gd, un, uk, i, j, k);
+    R xrt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr
+          + (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth;
+    R xrp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr
+          + (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * h * ir * is * g.idph;
+    R xtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * h * ir * g.idth
+          + (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * h * ir * is * g.idph;
+    R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
+    accp += -mu * (gm - R(1)) * cross;
     accT += -mu * c.beta[t] * cross;
+    double Np = (double)ap * divu + (double)accp, NT = (double)aT * divu + (double)accT;
     double sp = has_src ? src.f[0][t] : 0.0, sT = has_src ? src.f[4][t] : 0.0;
-    R.f[0][t] = -(uk.f[0][t] - un.f[0][t]) - tau * (accp - sp);
-    R.f[4][t] = -(uk.f[4][t] - un.f[4][t]) - tau * (accT - sT);
+    Rout.f[0][t] = (R)(-(uk.f[0][t] - un.f[0][t]) - tau * (Np - sp));
+    Rout.f[4][t] = (R)(-(uk.f[4][t] - un.f[4][t]) - tau * (NT - sT));
   }
 
   // ---- r-momentum on r-face i (interior faces 1..nr-1)
   if (i >= 1) {
     long id = IRf(g, i, j, k);
-    double wp[2], wu[3], w[3];
+    R wp[2], wu[3], w[3];
     row_f(g, P, c, UR, 0, i, j, k, wp, wu);
-    double acc = wp[0] * cval(g, Pp, g.bgp, i - 1, j, k) + wp[1] * cval(g, Pp, g.bgp, i, j, k)
-               + wu[0] * UR[IRf(g, i - 1, j, k)] + wu[1] * UR[id] + wu[2] * UR[IRf(g, i + 1, j, k)];
+    R acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i - 1, j, k))
+          + wu[0] * UR[IRf(g, i - 1, j, k)] + wu[1] * UR[id] + wu[2] * UR[IRf(g, i + 1, j, k)];
     row_s(g, P, c, ub, 0, 1, i, j, k, w);
     acc += w[0] * vr(g, UR, i, j - 1, k) + w[1] * UR[id] + w[2] * vr(g, UR, i, j + 1, k);
     row_s(g, P, c, ub, 0, 2, i, j, k, w);
     acc += w[0] * vr(g, UR, i, j, k - 1) + w[1] * UR[id] + w[2] * vr(g, UR, i, j, k + 1);
+    // hydrostatic part: (1/rho_f) d p_ref/dr + g = (1 - b) e + g b, b = 1 - rho_ref,f / rho_f
+    long c0 = IC(g, i - 1, j, k), c1 = IC(g, i, j, k);
+    R bf = (c.drho[c0] + c.drho[c1]) / (c.rho[c0] + c.rho[c1]);
+    R e = g.ehyd[i];
+    acc += (R(1) - bf) * e + (R)P.g * bf;
     // D_M
-    double irf = g.irf[i], s = g.sc[j];
-    double irh = 2.0 / (rho_at(g, c, i - 1, j, k) + rho_at(g, c, i, j, k));
-    double utf = 0.5 * (ht(g, UT, i - 1, j, k) + ht(g, UT, i, j, k));
-    double upf = 0.5 * (hp(g, UP, i - 1, j, k) + hp(g, UP, i, j, k));
-    double Q[2];
+    R irf = g.irf[i], s = g.sc[j];
+    R irh = R(2) / (c.rho[c0] + c.rho[c1]);
+    R utf = h * (ht(g, UT, i - 1, j, k) + ht(g, UT, i, j, k));
+    R upf = h * (hp(g, UP, i - 1, j, k) + hp(g, UP, i, j, k));
+    R Q[2];
     for (int q = 0; q < 2; q++) {
       int m = i - 1 + q;
       Q[q] = (g.sf[j + 1] * UT[ITf(g, m, j + 1, k)] - g.sf[j] * UT[ITf(g, m, j, k)]) * g.irc[m] * is * g.idth
            + (vp(g, UP, m, j, k + 1) - vp(g, UP, m, j, k)) * g.irc[m] * is * g.idph;
     }
-    acc += -utf * utf * irf - upf * upf * irf + 2.0 * mu * irh * UR[id] * irf * irf - 2.0 * om * s * upf
-         - mu * irh * (1.0 / 3.0) * g.idr * (Q[1] - Q[0]) + mu * irh * irf * (Q[0] + Q[1]);
+    acc += -utf * utf * irf - upf * upf * irf + R(2) * mu * irh * UR[id] * irf * irf - R(2) * om * s * upf
+         - mu * irh * R(1.0 / 3.0) * g.idr * (Q[1] - Q[0]) + mu * irh * irf * (Q[0] + Q[1]);
     double sv = has_src ? src.f[1][id] : 0.0;
-    R.f[1][id] = -(uk.f[1][id] - un.f[1][id]) - tau * (acc + P.g - sv);
+    Rout.f[1][id] = (R)(-(uk.f[1][id] - un.f[1][id]) - tau * ((double)acc - sv));
   } else {
-    R.f[1][IRf(g, 0, j, k)] = 0.0;
+    Rout.f[1][IRf(g, 0, j, k)] = R(0);
   }
-  if (i == g.nr - 1) R.f[1][IRf(g, g.nr, j, k)] = 0.0;
+  if (i == g.nr - 1) Rout.f[1][IRf(g, g.nr, j, k)] = R(0);
 
   // ---- theta-momentum on theta-face j (interior faces 1..nt-1)
   if (j >= 1) {
     long id = ITf(g, i, j, k);
-    double wp[2], wu[3], w[3];
+    R wp[2], wu[3], w[3];
     row_f(g, P, c, UT, 1, i, j, k, wp, wu);
-    double acc = wp[0] * cval(g, Pp, g.bgp, i, j - 1, k) + wp[1] * cval(g, Pp, g.bgp, i, j, k)
-               + wu[0] * UT[ITf(g, i, j - 1, k)] + wu[1] * UT[id] + wu[2] * UT[ITf(g, i, j + 1, k)];
+    R acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j - 1, k))
+          + wu[0] * UT[ITf(g, i, j - 1, k)] + wu[1] * UT[id] + wu[2] * UT[ITf(g, i, j + 1, k)];
     row_s(g, P, c, ub, 1, 0, i, j, k, w);
     acc += w[0] * vt(g, UT, i - 1, j, k) + w[1] * UT[id] + w[2] * vt(g, UT, i + 1, j, k);
     row_s(g, P, c, ub, 1, 2, i, j, k, w);
     acc += w[0] * vt(g, UT, i, j, k - 1) + w[1] * UT[id] + w[2] * vt(g, UT, i, j, k + 1);
-    double isfj = g.isf[j], cfj = g.cf[j], cotf = g.cotf[j];
-    double irh = 2.0 / (rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
-    double ubt = UT[id];
-    double upf = 0.5 * (hp(g, UP, i, j - 1, k) + hp(g, UP, i, j, k));
-    double vrf = 0.5 * (hr(g, UR, i, j - 1, k) + hr(g, UR, i, j, k));
-    double Dr[2], Dp[2], dpf = 0.0;
+    R isfj = g.isf[j], cfj = g.cf[j], cotf = g.cotf[j];
+    R irh = R(2) / (rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
+    R ubt = UT[id];
+    R upf = h * (hp(g, UP, i, j - 1, k) + hp(g, UP, i, j, k));
+    R vrf = h * (hr(g, UR, i, j - 1, k) + hr(g, UR, i, j, k));
+    R Dr[2], Dp[2], dpf = R(0);
     for (int q = 0; q < 2; q++) {
       int m = j - 1 + q;
       Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * UR[IRf(g, i + 1, m, k)] - g.rf[i] * g.rf[i] * UR[IRf(g, i, m, k)])
             * ir * ir * g.idr;
-      double dv = vp(g, UP, i, m, k + 1) - vp(g, UP, i, m, k);
+      R dv = vp(g, UP, i, m, k + 1) - vp(g, UP, i, m, k);
       Dp[q] = dv * ir * g.isc[m] * g.idph;
-      dpf += 0.5 * dv * g.idph;
+      dpf += h * dv * g.idph;
     }
-    acc += ubt * vrf * ir - upf * upf * cotf * ir + mu * irh * ubt * ir * ir * isfj * isfj - 2.0 * om * cfj * upf
-         - mu * irh * (1.0 / 3.0) * ir * g.idth * ((Dr[1] - Dr[0]) + (Dp[1] - Dp[0]))
-         - mu * irh * (2.0 * ir * ir * g.idth * (hr(g, UR, i, j, k) - hr(g, UR, i, j - 1, k))
-                       - 2.0 * cfj * ir * ir * isfj * isfj * dpf);
+    acc += ubt * vrf * ir - upf * upf * cotf * ir + mu * irh * ubt * ir * ir * isfj * isfj - R(2) * om * cfj * upf
+         - mu * irh * R(1.0 / 3.0) * ir * g.idth * ((Dr[1] - Dr[0]) + (Dp[1] - Dp[0]))
+         - mu * irh * (R(2) * ir * ir * g.idth * (hr(g, UR, i, j, k) - hr(g, UR, i, j - 1, k))
+                       - R(2) * cfj * ir * ir * isfj * isfj * dpf);
     double sv = has_src ? src.f[2][id] : 0.0;
-    R.f[2][id] = -(uk.f[2][id] - un.f[2][id]) - tau * (acc - sv);
+    Rout.f[2][id] = (R)(-(uk.f[2][id] - un.f[2][id]) - tau * ((double)acc - sv));
   } else {
-    R.f[2][ITf(g, i, 0, k)] = 0.0;
+    Rout.f[2][ITf(g, i, 0, k)] = R(0);
   }
-  if (j == g.nt - 1) R.f[2][ITf(g, i, g.nt, k)] = 0.0;
+  if (j == g.nt - 1) Rout.f[2][ITf(g, i, g.nt, k)] = R(0);
 
   // ---- phi-momentum on phi-face k (interior faces, or every face if periodic)
   if (k >= 1 || g.per) {
     long id = IPf(g, i, j, k);
-    double wp[2], wu[3], w[3];
+    R wp[2], wu[3], w[3];
     row_f(g, P, c, UP, 2, i, j, k, wp, wu);
-    double acc = wp[0] * cval(g, Pp, g.bgp, i, j, k - 1) + wp[1] * cval(g, Pp, g.bgp, i, j, k)
-               + wu[0] * vp(g, UP, i, j, k - 1) + wu[1] * UP[id] + wu[2] * vp(g, UP, i, j, k + 1);
+    R acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j, k - 1))
+          + wu[0] * vp(g, UP, i, j, k - 1) + wu[1] * UP[id] + wu[2] * vp(g, UP, i, j, k + 1);
     row_s(g, P, c, ub, 2, 0, i, j, k, w);
     acc += w[0] * vp(g, UP, i - 1, j, k) + w[1] * UP[id] + w[2] * vp(g, UP, i + 1, j, k);
     row_s(g, P, c, ub, 2, 1, i, j, k, w);
     acc += w[0] * vp(g, UP, i, j - 1, k) + w[1] * UP[id] + w[2] * vp(g, UP, i, j + 1, k);
-    double s = g.sc[j], cj = g.cc[j];
-    double irh = 2.0 / (rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
-    double ubp = UP[id];
-    double vrf = 0.5 * (hr(g, UR, i, j, k - 1) + hr(g, UR, i, j, k));
-    double vtf = 0.5 * (ht(g, UT, i, j, k - 1) + ht(g, UT, i, j, k));
-    double Dr[2], Dt[2];
+    R s = g.sc[j], cj = g.cc[j];
+    R irh = R(2) / (rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
+    R ubp = UP[id];
+    R vrf = h * (hr(g, UR, i, j, k - 1) + hr(g, UR, i, j, k));
+    R vtf = h * (ht(g, UT, i, j, k - 1) + ht(g, UT, i, j, k));
+    R Dr[2], Dt[2];
     for (int q = 0; q < 2; q++) {
       int m = k - 1 + q;
       Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * vr(g, UR, i + 1, j, m) - g.rf[i] * g.rf[i] * vr(g, UR, i, j, m))
             * ir * ir * g.idr;
       Dt[q] = (g.sf[j + 1] * vt(g, UT, i, j + 1, m) - g.sf[j] * vt(g, UT, i, j, m)) * ir * is * g.idth;
     }
-    acc += ubp * vtf * cot * ir + ubp * vrf * ir + mu * irh * ubp * ir * ir * is * is + 2.0 * om * (cj * vtf + s * vrf)
-         - mu * irh * (1.0 / 3.0) * ir * is * g.idph * ((Dr[1] - Dr[0]) + (Dt[1] - Dt[0]))
-         - mu * irh * (2.0 * ir * ir * is * g.idph * (hr(g, UR, i, j, k) - hr(g, UR, i, j, k - 1))
-                       + 2.0 * cj * ir * ir * is * is * g.idph * (ht(g, UT, i, j, k) - ht(g, UT, i, j, k - 1)));
+    acc += ubp * vtf * cot * ir + ubp * vrf * ir + mu * irh * ubp * ir * ir * is * is + R(2) * om * (cj * vtf + s * vrf)
+         - mu * irh * R(1.0 / 3.0) * ir * is * g.idph * ((Dr[1] - Dr[0]) + (Dt[1] - Dt[0]))
+         - mu * irh * (R(2) * ir * ir * is * g.idph * (hr(g, UR, i, j, k) - hr(g, UR, i, j, k - 1))
+                       + R(2) * cj * ir * ir * is * is * g.idph * (ht(g, UT, i, j, k) - ht(g, UT, i, j, k - 1)));
     double sv = has_src ? src.f[3][id] : 0.0;
-    R.f[3][id] = -(uk.f[3][id] - un.f[3][id]) - tau * (acc - sv);
+    Rout.f[3][id] = (R)(-(uk.f[3][id] - un.f[3][id]) - tau * ((double)acc - sv));
   } else {
-    R.f[3][IPf(g, i, j, 0)] = 0.0;
+    Rout.f[3][IPf(g, i, j, 0)] = R(0);
   }
-  if (!g.per && k == g.np - 1) R.f[3][IPf(g, i, j, g.np)] = 0.0;
+  if (!g.per && k == g.np - 1) Rout.f[3][IPf(g, i, j, g.np)] = R(0);
 }
 
 // ------------------------------------------------------------ line solvers
 
-__device__ __forceinline__ bool inv3(const double* S, double* I) {
-  double c00 = S[4] * S[8] - S[5] * S[7];
-  double c01 = S[5] * S[6] - S[3] * S[8];
-  double c02 = S[3] * S[7] - S[4] * S[6];
-  double det = S[0] * c00 + S[1] * c01 + S[2] * c02;
-  if (det == 0.0 || !isfinite(det)) return false;
-  double id = 1.0 / det;
+template <typename R>
+__device__ __forceinline__ bool inv3(const R* S, R* I) {
+  R c00 = S[4] * S[8] - S[5] * S[7];
+  R c01 = S[5] * S[6] - S[3] * S[8];
+  R c02 = S[3] * S[7] - S[4] * S[6];
+  R det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+  if (det == R(0) || !isfinite(det)) return false;
+  R id = R(1) / det;
   I[0] = c00 * id; I[3] = c01 * id; I[6] = c02 * id;
   I[1] = (S[2] * S[7] - S[1] * S[8]) * id;
   I[4] = (S[0] * S[8] - S[2] * S[6]) * id;
@@ -241,69 +295,73 @@ __device__ __forceinline__ void line_pos(int d, int a, int b, int m, int& i, int
   else { i = a; j = b; k = m; }
 }
 
-__device__ __forceinline__ long face_idx(const Geo& g, int d, int i, int j, int k) {
+template <typename G>
+__device__ __forceinline__ long face_idx(const G& g, int d, int i, int j, int k) {
   return d == 0 ? IRf(g, i, j, k) : d == 1 ? ITf(g, i, j, k) : IPf(g, i, j, k);
 }
 
-// Assemble block m of (I + h D_d) on the line (a, b); h = tau/2.
-__device__ void assemble_block(const Geo& g, const Par& P, const Coef& c, const CF& ub, int d, int n, int cyc, int m,
-                               int i, int j, int k, double h, double* A, double* B, double* C) {
-  double wp[3], wT[3], wu[2];
+// Assemble block m of (I + h D_d) on a line; h = tau/2.
+template <typename R>
+__device__ void assemble_block(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int d, int n, int cyc,
+                               int m, int i, int j, int k, R h, R* A, R* B, R* C) {
+  RowC<R> w;
 #pragma unroll
-  for (int q = 0; q < 9; q++) { A[q] = 0.0; B[q] = 0.0; C[q] = 0.0; }
-  row_c(g, P, c, d, 0, i, j, k, wp, wT, wu);
-  A[0] = h * wp[0]; A[1] = h * wT[0]; A[2] = h * wu[0];
-  B[0] = h * wp[1]; B[1] = h * wT[1]; B[2] = h * wu[1];
-  C[0] = h * wp[2]; C[1] = h * wT[2];
-  row_c(g, P, c, d, 1, i, j, k, wp, wT, wu);
-  A[4] = h * wT[0]; A[5] = h * wu[0];
-  B[4] = h * wT[1]; B[5] = h * wu[1];
-  C[4] = h * wT[2];
+  for (int q = 0; q < 9; q++) { A[q] = R(0); B[q] = R(0); C[q] = R(0); }
+  row_c(g, P, c, d, 0, i, j, k, w);
+  A[0] = h * w.wp[0]; A[1] = h * w.wT[0]; A[2] = h * (w.a * w.gd[0] + w.wv[0]);
+  B[0] = h * w.wp[1]; B[1] = h * w.wT[1]; B[2] = h * (w.a * w.gd[1] + w.wv[1]);
+  C[0] = h * w.wp[2]; C[1] = h * w.wT[2];
+  row_c(g, P, c, d, 1, i, j, k, w);
+  A[4] = h * w.wT[0]; A[5] = h * (w.a * w.gd[0] + w.wv[0]);
+  B[4] = h * w.wT[1]; B[5] = h * (w.a * w.gd[1] + w.wv[1]);
+  C[4] = h * w.wT[2];
   if (m < n - 1 || cyc) {
     int fi = i, fj = j, fk = k;
     if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = (m + 1 == n) ? 0 : m + 1;
-    double fp[2], fu[3];
+    R fp[2], fu[3];
     row_f(g, P, c, ub.f[1 + d], d, fi, fj, fk, fp, fu);
     A[8] = h * fu[0];
     B[6] = h * fp[0]; B[8] = h * fu[1];
     C[6] = h * fp[1]; C[8] = h * fu[2];
   }
-  B[0] += 1.0; B[4] += 1.0; B[8] += 1.0;
+  B[0] += R(1); B[4] += R(1); B[8] += R(1);
   if (!cyc) {
     if (m == 0) {
       B[0] += A[0]; B[1] += A[1]; B[3] += A[3]; B[4] += A[4];
 #pragma unroll
-      for (int q = 0; q < 9; q++) A[q] = 0.0;
+      for (int q = 0; q < 9; q++) A[q] = R(0);
     }
     if (m == n - 1) {
       B[0] += C[0]; B[1] += C[1]; B[3] += C[3]; B[4] += C[4];
 #pragma unroll
-      for (int q = 0; q < 9; q++) C[q] = 0.0;
-      B[2] = 0.0; B[5] = 0.0;
-      A[8] = 0.0; B[6] = 0.0; B[7] = 0.0; B[8] = 1.0;
+      for (int q = 0; q < 9; q++) C[q] = R(0);
+      B[2] = R(0); B[5] = R(0);
+      A[8] = R(0); B[6] = R(0); B[7] = R(0); B[8] = R(1);
     }
   }
 }
 
+template <typename R>
 struct SweepArgs {
-  Geo g; Par P; Coef c; CF ub;
-  int d; double h;
-  CF rhs;              // right-hand side fields
-  MF x;                // output increments (mode 0)
-  int update;          // mode 1: uk = base + x, accumulate norms
-  CF base; MF uk;
-  double* scr;         // scratch
-  long scr_off[3];     // offsets of the three kinds
-  long nl[3];          // lines per kind
+  Geo<R> g; Par P; Coef<R> c; CF<R> ub;
+  int d; R h;
+  CF<R> rhs;              // right-hand side fields
+  MF<R> x;                // output increments (mode 0)
+  int update;             // mode 1: uk = base + x (FP64), accumulate norms
+  CF<double> base; MF<double> uk;
+  R* scr;                 // scratch
+  long scr_off[3];        // offsets of the three kinds
+  long nl[3];             // lines per kind
   int a0[3], nb[3], b0[3];
-  double* acc;         // 5 sums of squares (mode 1)
+  double* acc;            // 5 sums of squares (mode 1)
   int* flag;
 };
 
 // store a value of field f at flat index idx: x (mode 0) or uk = base + v (mode 1)
-__device__ __forceinline__ void put(const SweepArgs& A, int f, long idx, double v, double* ss, int* bad) {
+template <typename R>
+__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, long idx, double v, double* ss, int* bad) {
   if (!A.update) {
-    A.x.f[f][idx] = v;
+    A.x.f[f][idx] = (R)v;
   } else {
     double nv = A.base.f[f][idx] + v;
     if (!isfinite(nv)) *bad |= FLAG_NONFINITE;
@@ -312,33 +370,34 @@ __device__ __forceinline__ void put(const SweepArgs& A, int f, long idx, double 
   }
 }
 // wall face of field f: x = 0, or uk = base (mode 1)
-__device__ __forceinline__ void put_wall(const SweepArgs& A, int f, long idx) {
-  if (!A.update) A.x.f[f][idx] = 0.0;
+template <typename R>
+__device__ __forceinline__ void put_wall(const SweepArgs<R>& A, int f, long idx) {
+  if (!A.update) A.x.f[f][idx] = R(0);
   else A.uk.f[f][idx] = A.base.f[f][idx];
 }
 
-__device__ void block_line(const SweepArgs& S, long line, int a, int b, double* ss, int* bad) {
-  const Geo& g = S.g;
+template <typename R>
+__device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, double* ss, int* bad) {
+  const Geo<R>& g = S.g;
   int d = S.d;
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
   int cyc = (d == 2 && g.per);
   long nl = S.nl[0];
-  double* scr = S.scr + S.scr_off[0];
+  R* scr = S.scr + S.scr_off[0];
   const int W = cyc ? 21 : 12;  // C' (9) + d' (3 per right-hand side)
   const int NR = cyc ? 4 : 1;
-  double Cp[9], dp[12];
-  double GiA[9];                // cyclic: Gam^{-1} A_0
-  double Gam[9];
+  R Cp[9], dp[12];
+  R GiA[9];                     // cyclic: Gam^{-1} A_0
   for (int m = 0; m < n; m++) {
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    double A[9], B[9], C[9];
+    R A[9], B[9], C[9];
     assemble_block(g, S.P, S.c, S.ub, d, n, cyc, m, i, j, k, S.h, A, B, C);
-    double rr[12];
+    R rr[12];
     long ic = IC(g, i, j, k);
     rr[0] = S.rhs.f[0][ic];
     rr[NR] = S.rhs.f[4][ic];
-    double ru = 0.0;
+    R ru = R(0);
     if (m < n - 1 || cyc) {
       int fi = i, fj = j, fk = k;
       if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = (m + 1 == n) ? 0 : m + 1;
@@ -348,10 +407,10 @@ __device__ void block_line(const SweepArgs& S, long line, int a, int b, double* 
     if (cyc) {
       // right-hand-side columns 1..3 of U = [Gam; 0; ..; C_{n-1}]
       for (int r = 0; r < 3; r++)
-        for (int q = 0; q < 3; q++) rr[r * NR + 1 + q] = 0.0;
+        for (int q = 0; q < 3; q++) rr[r * NR + 1 + q] = R(0);
       if (m == 0) {
+        R Gam[9], Gi[9];
         for (int q = 0; q < 9; q++) Gam[q] = -B[q];
-        double Gi[9];
         if (!inv3(Gam, Gi)) { *bad |= FLAG_SINGULAR; return; }
         for (int r = 0; r < 3; r++)
           for (int q = 0; q < 3; q++) GiA[r * 3 + q] = Gi[r * 3] * A[q] + Gi[r * 3 + 1] * A[3 + q] + Gi[r * 3 + 2] * A[6 + q];
@@ -368,7 +427,7 @@ __device__ void block_line(const SweepArgs& S, long line, int a, int b, double* 
       }
     }
     // S = B - A C'_{m-1};  y = rr - A d'_{m-1}
-    double Sm[9], y[12];
+    R Sm[9], y[12];
     if (m == 0) {
       for (int q = 0; q < 9; q++) Sm[q] = B[q];
       for (int q = 0; q < 3 * NR; q++) y[q] = rr[q];
@@ -380,9 +439,8 @@ __device__ void block_line(const SweepArgs& S, long line, int a, int b, double* 
           y[r * NR + q] = rr[r * NR + q] - (A[r * 3] * dp[q] + A[r * 3 + 1] * dp[NR + q] + A[r * 3 + 2] * dp[2 * NR + q]);
       }
     }
-    double Si[9];
+    R Si[9];
     if (!inv3(Sm, Si)) { *bad |= FLAG_SINGULAR; return; }
-    // the last block has no right neighbour on a non-cyclic line: C = 0
     for (int r = 0; r < 3; r++) {
       for (int q = 0; q < 3; q++)
         Cp[r * 3 + q] = Si[r * 3] * C[q] + Si[r * 3 + 1] * C[3 + q] + Si[r * 3 + 2] * C[6 + q];
@@ -390,23 +448,22 @@ __device__ void block_line(const SweepArgs& S, long line, int a, int b, double* 
         dp[r * NR + q] = Si[r * 3] * y[q] + Si[r * 3 + 1] * y[NR + q] + Si[r * 3 + 2] * y[2 * NR + q];
     }
     if (m < n - 1) {
-      double* s = scr + (long)m * W * nl + line;
+      R* s = scr + (long)m * W * nl + line;
       for (int q = 0; q < 9; q++) s[(long)q * nl] = Cp[q];
       for (int q = 0; q < 3 * NR; q++) s[(long)(9 + q) * nl] = dp[q];
     }
   }
   // back substitution, all NR columns
-  double xs[12];
+  R xs[12];
   for (int q = 0; q < 3 * NR; q++) xs[q] = dp[q];
-  double fcor[3] = {0.0, 0.0, 0.0};
-  double x0[12];
+  R x0[12];
   for (int m = n - 1; m >= 0; m--) {
     if (m < n - 1) {
-      const double* s = scr + (long)m * W * nl + line;
-      double C_[9], d_[12];
+      const R* s = scr + (long)m * W * nl + line;
+      R C_[9], d_[12];
       for (int q = 0; q < 9; q++) C_[q] = s[(long)q * nl];
       for (int q = 0; q < 3 * NR; q++) d_[q] = s[(long)(9 + q) * nl];
-      double xn[12];
+      R xn[12];
       for (int r = 0; r < 3; r++)
         for (int q = 0; q < NR; q++)
           xn[r * NR + q] = d_[r * NR + q] - (C_[r * 3] * xs[q] + C_[r * 3 + 1] * xs[NR + q] + C_[r * 3 + 2] * xs[2 * NR + q]);
@@ -416,12 +473,12 @@ __device__ void block_line(const SweepArgs& S, long line, int a, int b, double* 
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
       long ic = IC(g, i, j, k);
-      put(S, 0, ic, xs[0], ss, bad);
-      put(S, 4, ic, xs[1], ss, bad);
+      put(S, 0, ic, (double)xs[0], ss, bad);
+      put(S, 4, ic, (double)xs[1], ss, bad);
       if (m < n - 1) {
         int fi = i, fj = j, fk = k;
         if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = m + 1;
-        put(S, 1 + d, face_idx(g, d, fi, fj, fk), xs[2], ss, bad);
+        put(S, 1 + d, face_idx(g, d, fi, fj, fk), (double)xs[2], ss, bad);
       } else {
         int fi = i, fj = j, fk = k;
         if (d == 0) fi = n; else if (d == 1) fj = n; else fk = n;
@@ -431,33 +488,31 @@ __device__ void block_line(const SweepArgs& S, long line, int a, int b, double* 
         put_wall(S, 1 + d, face_idx(g, d, gi, gj, gk));
       }
     } else {
-      // keep x (all columns) in scratch d'-slots for the Woodbury combination
-      double* s = scr + (long)m * W * nl + line;
+      // keep x (all columns) in the d'-slots for the Woodbury combination
+      R* s = scr + (long)m * W * nl + line;
       for (int q = 0; q < 3 * NR; q++) s[(long)(9 + q) * nl] = xs[q];
       if (m == 0) for (int q = 0; q < 12; q++) x0[q] = xs[q];
     }
   }
   if (cyc) {
-    // V^T y = y_0 + GiA y_{n-1};  V^T Z = Z_0 + GiA Z_{n-1};  f = (I + V^T Z)^{-1} V^T y
-    const double* sl = scr + (long)(n - 1) * W * nl + line;
-    double xl[12];
-    for (int q = 0; q < 12; q++) xl[q] = sl[(long)(9 + q) * nl];
-    double vy[3], vz[9];
+    // V^T y = y_0 + GiA y_{n-1};  V^T Z = Z_0 + GiA Z_{n-1};  f = (I + V^T Z)^{-1} V^T y  (FP64)
+    const R* sl = scr + (long)(n - 1) * W * nl + line;
+    double xl[12], vy[3], vz[9], vi[9], fcor[3];
+    for (int q = 0; q < 12; q++) xl[q] = (double)sl[(long)(9 + q) * nl];
     for (int r = 0; r < 3; r++) {
-      vy[r] = x0[r * 4] + GiA[r * 3] * xl[0] + GiA[r * 3 + 1] * xl[4] + GiA[r * 3 + 2] * xl[8];
+      vy[r] = (double)x0[r * 4] + (double)GiA[r * 3] * xl[0] + (double)GiA[r * 3 + 1] * xl[4] + (double)GiA[r * 3 + 2] * xl[8];
       for (int q = 0; q < 3; q++)
-        vz[r * 3 + q] = x0[r * 4 + 1 + q] + GiA[r * 3] * xl[1 + q] + GiA[r * 3 + 1] * xl[5 + q] + GiA[r * 3 + 2] * xl[9 + q]
-                      + (r == q ? 1.0 : 0.0);
+        vz[r * 3 + q] = (double)x0[r * 4 + 1 + q] + (double)GiA[r * 3] * xl[1 + q] + (double)GiA[r * 3 + 1] * xl[5 + q]
+                      + (double)GiA[r * 3 + 2] * xl[9 + q] + (r == q ? 1.0 : 0.0);
     }
-    double vi[9];
     if (!inv3(vz, vi)) { *bad |= FLAG_SINGULAR; return; }
     for (int r = 0; r < 3; r++) fcor[r] = vi[r * 3] * vy[0] + vi[r * 3 + 1] * vy[1] + vi[r * 3 + 2] * vy[2];
     for (int m = 0; m < n; m++) {
-      const double* s = scr + (long)m * W * nl + line;
+      const R* s = scr + (long)m * W * nl + line;
       double xv[3];
       for (int r = 0; r < 3; r++) {
-        xv[r] = s[(long)(9 + r * 4) * nl];
-        for (int q = 0; q < 3; q++) xv[r] -= s[(long)(9 + r * 4 + 1 + q) * nl] * fcor[q];
+        xv[r] = (double)s[(long)(9 + r * 4) * nl];
+        for (int q = 0; q < 3; q++) xv[r] -= (double)s[(long)(9 + r * 4 + 1 + q) * nl] * fcor[q];
       }
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
@@ -479,9 +534,10 @@ __device__ __forceinline__ int trans_comp(int d, int kind) {
 
 // output of a transverse line value at cell m, plus the wall faces of that
 // component next to the first / last line
-__device__ __forceinline__ void scalar_put(const SweepArgs& S, int cc, int i, int j, int k, double v, double* ss,
+template <typename R>
+__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, double v, double* ss,
                                            int* bad) {
-  const Geo& g = S.g;
+  const Geo<R>& g = S.g;
   put(S, 1 + cc, face_idx(g, cc, i, j, k), v, ss, bad);
   int lo = (cc == 0) ? (i == 1) : (cc == 1) ? (j == 1) : (k == 1);
   int hi = (cc == 0) ? (i == g.nr - 1) : (cc == 1) ? (j == g.nt - 1) : (k == g.np - 1);
@@ -498,81 +554,84 @@ __device__ __forceinline__ void scalar_put(const SweepArgs& S, int cc, int i, in
   }
 }
 
-__device__ void scalar_line(const SweepArgs& S, int kind, long line, int a, int b, double* ss, int* bad) {
-  const Geo& g = S.g;
+template <typename R>
+__device__ void scalar_line(const SweepArgs<R>& S, int kind, long line, int a, int b, double* ss, int* bad) {
+  const Geo<R>& g = S.g;
   int d = S.d;
   int cc = trans_comp(d, kind);
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
   int cyc = (d == 2 && g.per);
   long nl = S.nl[kind];
-  double* scr = S.scr + S.scr_off[kind];
-  const double* rhs = S.rhs.f[1 + cc];
-  double cp = 0.0, dy = 0.0, dz = 0.0;
-  double a0 = 0.0, gam = 1.0;
+  R* scr = S.scr + S.scr_off[kind];
+  const R* rhs = S.rhs.f[1 + cc];
+  R cp = R(0), dy = R(0), dz = R(0);
+  R a0 = R(0), gam = R(1);
   for (int m = 0; m < n; m++) {
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    double w[3];
+    R w[3];
     row_s(g, S.P, S.c, S.ub, cc, d, i, j, k, w);
-    double am = S.h * w[0], bm = 1.0 + S.h * w[1], cm = S.h * w[2];
-    double zr = 0.0;
+    R am = S.h * w[0], bm = R(1) + S.h * w[1], cm = S.h * w[2];
+    R zr = R(0);
     if (!cyc) {
-      if (m == 0) { bm -= am; am = 0.0; }
-      if (m == n - 1) { bm -= cm; cm = 0.0; }
+      if (m == 0) { bm -= am; am = R(0); }
+      if (m == n - 1) { bm -= cm; cm = R(0); }
     } else {
       // Sherman-Morrison split: gam = -b_0, u = [gam, 0, .., c_{n-1}], v = [1, 0, .., a_0/gam]
-      if (m == 0) { a0 = am; gam = -bm; bm -= gam; zr = gam; am = 0.0; }
-      if (m == n - 1) { bm -= a0 * cm / gam; zr = cm; cm = 0.0; }
+      if (m == 0) { a0 = am; gam = -bm; bm -= gam; zr = gam; am = R(0); }
+      if (m == n - 1) { bm -= a0 * cm / gam; zr = cm; cm = R(0); }
     }
-    double r = rhs[face_idx(g, cc, i, j, k)];
-    double den = bm - am * cp;
-    if (den == 0.0 || !isfinite(den)) { *bad |= FLAG_SINGULAR; return; }
-    double iden = 1.0 / den;
+    R r = rhs[face_idx(g, cc, i, j, k)];
+    R den = bm - am * cp;
+    if (den == R(0) || !isfinite(den)) { *bad |= FLAG_SINGULAR; return; }
+    R iden = R(1) / den;
     cp = cm * iden;
     dy = (r - am * dy) * iden;
-    double* s = scr + (long)m * 3 * nl + line;
+    R* s = scr + (long)m * 3 * nl + line;
     s[0] = cp;
     s[nl] = dy;
     if (cyc) { dz = (zr - am * dz) * iden; s[2 * nl] = dz; }
   }
   if (!cyc) {
-    double xy = dy;
+    R xy = dy;
     for (int m = n - 1; m >= 0; m--) {
       if (m < n - 1) {
-        const double* t = scr + (long)m * 3 * nl + line;
+        const R* t = scr + (long)m * 3 * nl + line;
         xy = t[nl] - t[0] * xy;
       }
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
-      scalar_put(S, cc, i, j, k, xy, ss, bad);
+      scalar_put(S, cc, i, j, k, (double)xy, ss, bad);
     }
     return;
   }
-  // cyclic: back-substitute both columns, then combine
-  double xy = dy, xz = dz, yl = dy, zl = dz;
+  // cyclic: back-substitute both columns, then combine in FP64
+  R xy = dy, xz = dz, yl = dy, zl = dz;
   for (int m = n - 2; m >= 0; m--) {
-    double* t = scr + (long)m * 3 * nl + line;
+    R* t = scr + (long)m * 3 * nl + line;
     xy = t[nl] - t[0] * xy;
     xz = t[2 * nl] - t[0] * xz;
     t[nl] = xy;
     t[2 * nl] = xz;
   }
   {
-    double* t = scr + (long)(n - 1) * 3 * nl + line;
+    R* t = scr + (long)(n - 1) * 3 * nl + line;
     t[nl] = yl;
     t[2 * nl] = zl;
   }
-  double vy = xy + a0 / gam * yl, vz = xz + a0 / gam * zl;
+  double ag = (double)a0 / (double)gam;
+  double vy = (double)xy + ag * (double)yl, vz = (double)xz + ag * (double)zl;
   double f = vy / (1.0 + vz);
   for (int m = 0; m < n; m++) {
-    const double* t = scr + (long)m * 3 * nl + line;
+    const R* t = scr + (long)m * 3 * nl + line;
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    scalar_put(S, cc, i, j, k, t[nl] - f * t[2 * nl], ss, bad);
+    scalar_put(S, cc, i, j, k, (double)t[nl] - f * (double)t[2 * nl], ss, bad);
   }
 }
 
-__global__ void k_sweep(SweepArgs S) {
+template <typename R>
+__global__ void k_sweep(SweepArgs<R> S) {
   int kind = blockIdx.y;
   long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
   double ss[5] = {0, 0, 0, 0, 0};
@@ -595,28 +654,38 @@ __global__ void k_sweep(SweepArgs S) {
 
 // ============================================================== host side
 
+// Device buffers of one precision.
+template <typename R>
+struct Bufs {
+  R* metric;       // rc rf irc irf | sc sf isc isf cc cf cotc cotf (bulk type)
+  R* bgder;        // dbgp dbgT lapT rhoref (nr each) ehyd (nr+1)
+  R* Ub[5];
+  R* Rb[5];
+  R* X1[5];
+  R* coef;
+  R* scr;
+  Geo<R> g;
+  Coef<R> c;
+};
+
 struct sph_ctx {
   int dev;
   cudaStream_t st;
-  Geo g;
-  Par P;
   int prec;
+  Par P;
   size_t nf[5];
   long N;
-  double* metric;
-  double* bg;
+  double* bg;            // p_ref, T_ref (nr+2 each)
   double* U[2][5];
   int cur;
   int iterate_set;
-  double* Ub[5];
-  double* R[5];
-  double* X1[5];
   double* src[5];
-  double* coef;
-  Coef c;
-  double* scr;
-  double* acc;   // 5 sums + spare
+  double* acc;           // 5 sums + spare
   int* flag;
+  double* hmet;          // host copy of the FP64 metric tables
+  size_t nmet;
+  Bufs<double> d64;      // FP64 metric/background tables always; bulk buffers in FP64 mode
+  Bufs<float> d32;       // bulk buffers in mixed mode
   long long launches;
   long unknowns[5];
   // per-kernel timing
@@ -664,13 +733,19 @@ static void prof_free(sph_ctx* c) {
   c->ev = NULL; c->evkind = NULL; c->evcap = 0; c->nev = 0;
 }
 
+template <typename R>
+static void bufs_free(Bufs<R>& b) {
+  cudaFree(b.metric); cudaFree(b.bgder); cudaFree(b.coef); cudaFree(b.scr);
+  for (int f = 0; f < 5; f++) { cudaFree(b.Ub[f]); cudaFree(b.Rb[f]); cudaFree(b.X1[f]); }
+}
+
 static void free_all(sph_ctx* c) {
   prof_free(c);
-  cudaFree(c->metric); cudaFree(c->bg); cudaFree(c->coef); cudaFree(c->scr); cudaFree(c->acc); cudaFree(c->flag);
-  for (int f = 0; f < 5; f++) {
-    cudaFree(c->U[0][f]); cudaFree(c->U[1][f]); cudaFree(c->Ub[f]); cudaFree(c->R[f]); cudaFree(c->X1[f]);
-    cudaFree(c->src[f]);
-  }
+  bufs_free(c->d64);
+  bufs_free(c->d32);
+  cudaFree(c->bg); cudaFree(c->acc); cudaFree(c->flag);
+  for (int f = 0; f < 5; f++) { cudaFree(c->U[0][f]); cudaFree(c->U[1][f]); cudaFree(c->src[f]); }
+  free(c->hmet);
 }
 
 extern "C" void sph_destroy(sph_ctx* ctx) {
@@ -684,6 +759,105 @@ extern "C" void sph_destroy(sph_ctx* ctx) {
   free(ctx);
 }
 
+// metric tables: 4 (nr+1) radial + 8 (nt+1) polar values
+static void fill_metric(const sph_grid* gr, double* h, int nr, int nt, double dr, double dth) {
+  double* rc = h; double* rf = rc + (nr + 1); double* irc = rf + (nr + 1); double* irf = irc + (nr + 1);
+  double* sc = irf + (nr + 1); double* sf = sc + (nt + 1); double* isc = sf + (nt + 1); double* isf = isc + (nt + 1);
+  double* cc = isf + (nt + 1); double* cf = cc + (nt + 1); double* cotc = cf + (nt + 1); double* cotf = cotc + (nt + 1);
+  for (int i = 0; i < nr; i++) { rc[i] = gr->r1 + (i + 0.5) * dr; irc[i] = 1.0 / rc[i]; }
+  for (int i = 0; i <= nr; i++) { rf[i] = gr->r1 + i * dr; irf[i] = 1.0 / rf[i]; }
+  for (int j = 0; j < nt; j++) {
+    double t = gr->th1 + (j + 0.5) * dth;
+    sc[j] = sin(t); cc[j] = cos(t); isc[j] = 1.0 / sc[j]; cotc[j] = cc[j] / sc[j];
+  }
+  for (int j = 0; j <= nt; j++) {
+    double t = gr->th1 + j * dth;
+    sf[j] = sin(t); cf[j] = cos(t);
+  }
+  if (fabs(gr->th1) < 1e-14) sf[0] = 0.0;
+  if (fabs(gr->th2 - M_PI) < 1e-14) sf[nt] = 0.0;
+  for (int j = 0; j <= nt; j++) { isf[j] = sf[j] != 0.0 ? 1.0 / sf[j] : 0.0; cotf[j] = sf[j] != 0.0 ? cf[j] / sf[j] : 0.0; }
+}
+
+template <typename R>
+static void set_geo_ptrs(Bufs<R>& b, const Geo<double>& base, const double* bg, int nr, int nt) {
+  Geo<R>& g = b.g;
+  g.nr = base.nr; g.nt = base.nt; g.np = base.np; g.npf = base.npf; g.per = base.per;
+  g.dr = (R)base.dr; g.dth = (R)base.dth; g.dph = (R)base.dph;
+  g.idr = (R)base.idr; g.idth = (R)base.idth; g.idph = (R)base.idph;
+  R* m = b.metric;
+  g.rc = m; g.rf = m + (nr + 1); g.irc = m + 2 * (nr + 1); g.irf = m + 3 * (nr + 1);
+  R* tb = m + 4 * (nr + 1);
+  g.sc = tb; g.sf = tb + (nt + 1); g.isc = tb + 2 * (nt + 1); g.isf = tb + 3 * (nt + 1);
+  g.cc = tb + 4 * (nt + 1); g.cf = tb + 5 * (nt + 1); g.cotc = tb + 6 * (nt + 1); g.cotf = tb + 7 * (nt + 1);
+  g.bgp = bg; g.bgT = bg + (nr + 2);
+  g.dbgp = b.bgder; g.dbgT = b.bgder + nr; g.lapT = b.bgder + 2 * nr; g.rhoref = b.bgder + 3 * nr;
+  g.ehyd = b.bgder + 4 * nr;
+}
+
+template <typename R>
+static int bufs_alloc(Bufs<R>& b, size_t nmet, int nr, const size_t* nf, long N, size_t nscr, int bulk) {
+#define ALLOC(p, n) do { if (!cuda_ok(cudaMalloc((void**)&(p), (size_t)(n) * sizeof(R)))) return SPH_ERR_NOMEM; } while (0)
+  ALLOC(b.metric, nmet);
+  ALLOC(b.bgder, 5 * (size_t)nr + 1);
+  if (!bulk) return SPH_OK;
+  for (int f = 0; f < 5; f++) { ALLOC(b.Ub[f], nf[f]); ALLOC(b.Rb[f], nf[f]); ALLOC(b.X1[f], nf[f]); }
+  ALLOC(b.coef, (size_t)NCOEF * N);
+  ALLOC(b.scr, nscr);
+#undef ALLOC
+  R* q = b.coef;
+  Coef<R>& cf = b.c;
+  cf.Pb = q; cf.Tb = q + N; cf.rho = q + 2 * N; cf.drho = q + 3 * N; cf.beta = q + 4 * N; cf.uc0 = q + 5 * N;
+  cf.uc1 = q + 6 * N; cf.uc2 = q + 7 * N; cf.grr = q + 8 * N; cf.gtt = q + 9 * N; cf.gpp = q + 10 * N;
+  cf.srt = q + 11 * N; cf.srp = q + 12 * N; cf.stp = q + 13 * N;
+  return SPH_OK;
+}
+
+template <typename R>
+static int upload_tables(sph_ctx* c, Bufs<R>& b, const double* hmet, const double* hder, int nr) {
+  size_t nd = 5 * (size_t)nr + 1;
+  R* tm = (R*)malloc(c->nmet * sizeof(R));
+  R* td = (R*)malloc(nd * sizeof(R));
+  if (!tm || !td) { free(tm); free(td); return SPH_ERR_NOMEM; }
+  for (size_t q = 0; q < c->nmet; q++) tm[q] = (R)hmet[q];
+  for (size_t q = 0; q < nd; q++) td[q] = (R)hder[q];
+  int e = SPH_OK;
+  if (!cuda_ok(cudaMemcpy(b.metric, tm, c->nmet * sizeof(R), cudaMemcpyHostToDevice)) ||
+      !cuda_ok(cudaMemcpy(b.bgder, td, nd * sizeof(R), cudaMemcpyHostToDevice)))
+    e = SPH_ERR_CUDA;
+  free(tm); free(td);
+  return e;
+}
+
+// Background-derived tables (FP64 on the host, then in each bulk type).
+static int upload_background(sph_ctx* c, const double* pref, const double* Tref) {
+  const Geo<double>& g = c->d64.g;
+  int nr = g.nr;
+  const double* rc = c->hmet;
+  const double* rf = rc + (nr + 1);
+  double* der = (double*)calloc(5 * (size_t)nr + 1, sizeof(double));
+  if (!der) return SPH_ERR_NOMEM;
+  double* dbgp = der; double* dbgT = der + nr; double* lapT = der + 2 * nr; double* rhoref = der + 3 * nr;
+  double* ehyd = der + 4 * nr;
+  double Rg = c->P.Rg, pinf = c->P.pinf;
+  for (int i = 0; i < nr; i++) {
+    // index i+1 of the tables is centre i; 0 and nr+1 are the ghosts
+    dbgp[i] = pref[i + 2] - pref[i];
+    dbgT[i] = Tref[i + 2] - Tref[i];
+    double f0 = rf[i] * rf[i], f1 = rf[i + 1] * rf[i + 1];
+    lapT[i] = (f1 * (Tref[i + 2] - Tref[i + 1]) - f0 * (Tref[i + 1] - Tref[i])) / (rc[i] * rc[i] * g.dr * g.dr);
+    rhoref[i] = Tref[i + 1] != 0.0 ? (pref[i + 1] + pinf) / (Rg * Tref[i + 1]) : 0.0;
+  }
+  for (int i = 1; i < nr; i++) {
+    double rf_ = 0.5 * (rhoref[i - 1] + rhoref[i]);
+    ehyd[i] = rf_ != 0.0 ? (pref[i + 1] - pref[i]) / (g.dr * rf_) + c->P.g : c->P.g;
+  }
+  int e = upload_tables(c, c->d64, c->hmet, der, nr);
+  if (e == SPH_OK && c->prec == SPH_PREC_MIXED) e = upload_tables(c, c->d32, c->hmet, der, nr);
+  free(der);
+  return e;
+}
+
 extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream, sph_ctx** out) {
   if (!gr || !pa || !out) return SPH_ERR_ARG;
   *out = NULL;
@@ -692,13 +866,14 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   if (gr->th1 < 0 || gr->th2 > M_PI + 1e-12) return SPH_ERR_ARG;
   if (gr->periodic_phi && gr->nph < 3) return SPH_ERR_ARG;
   if (!(pa->gamma > 1) || !(pa->cv > 0) || !(pa->Pr > 0) || pa->mu < 0) return SPH_ERR_ARG;
-  if (pa->precision != SPH_PREC_FP64) return SPH_ERR_ARG;   /* mixed precision: separate entry */
+  if (pa->precision != SPH_PREC_FP64 && pa->precision != SPH_PREC_MIXED) return SPH_ERR_ARG;
   sph_ctx* c = (sph_ctx*)calloc(1, sizeof(sph_ctx));
   if (!c) return SPH_ERR_NOMEM;
   cudaGetDevice(&c->dev);
   c->st = (cudaStream_t)stream;
   c->prec = pa->precision;
-  Geo& g = c->g;
+  Geo<double> g;
+  memset(&g, 0, sizeof g);
   g.nr = gr->nr; g.nt = gr->nth; g.np = gr->nph; g.per = gr->periodic_phi ? 1 : 0;
   g.npf = g.per ? g.np : g.np + 1;
   g.dr = (gr->r2 - gr->r1) / g.nr; g.dth = (gr->th2 - gr->th1) / g.nt; g.dph = (gr->ph2 - gr->ph1) / g.np;
@@ -715,69 +890,46 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   c->unknowns[2] = (long)g.nr * (g.nt - 1) * g.np;
   c->unknowns[3] = (long)g.nr * g.nt * (g.per ? g.np : g.np - 1);
 
-  // metric tables on the host, then one copy
   int nr = g.nr, nt = g.nt;
-  size_t nmet = 4 * (size_t)(nr + 1) + 8 * (size_t)(nt + 1);
-  double* h = (double*)calloc(nmet, sizeof(double));
-  double* rc = h; double* rf = rc + (nr + 1); double* irc = rf + (nr + 1); double* irf = irc + (nr + 1);
-  double* sc = irf + (nr + 1); double* sf = sc + (nt + 1); double* isc = sf + (nt + 1); double* isf = isc + (nt + 1);
-  double* cc = isf + (nt + 1); double* cf = cc + (nt + 1); double* cotc = cf + (nt + 1); double* cotf = cotc + (nt + 1);
-  for (int i = 0; i < nr; i++) { rc[i] = gr->r1 + (i + 0.5) * g.dr; irc[i] = 1.0 / rc[i]; }
-  for (int i = 0; i <= nr; i++) { rf[i] = gr->r1 + i * g.dr; irf[i] = 1.0 / rf[i]; }
-  for (int j = 0; j < nt; j++) {
-    double t = gr->th1 + (j + 0.5) * g.dth;
-    sc[j] = sin(t); cc[j] = cos(t); isc[j] = 1.0 / sc[j]; cotc[j] = cc[j] / sc[j];
-  }
-  for (int j = 0; j <= nt; j++) {
-    double t = gr->th1 + j * g.dth;
-    sf[j] = sin(t); cf[j] = cos(t);
-  }
-  if (fabs(gr->th1) < 1e-14) sf[0] = 0.0;
-  if (fabs(gr->th2 - M_PI) < 1e-14) sf[nt] = 0.0;
-  for (int j = 0; j <= nt; j++) { isf[j] = sf[j] != 0.0 ? 1.0 / sf[j] : 0.0; cotf[j] = sf[j] != 0.0 ? cf[j] / sf[j] : 0.0; }
+  c->nmet = 4 * (size_t)(nr + 1) + 8 * (size_t)(nt + 1);
+  c->hmet = (double*)calloc(c->nmet, sizeof(double));
+  if (!c->hmet) { free(c); return SPH_ERR_NOMEM; }
+  fill_metric(gr, c->hmet, nr, nt, g.dr, g.dth);
+  const double* scs = c->hmet + 4 * (nr + 1);
   for (int j = 0; j < nt; j++)
-    if (!(sc[j] > 0)) { free(h); free(c); return SPH_ERR_ARG; }
+    if (!(scs[j] > 0)) { free(c->hmet); free(c); return SPH_ERR_ARG; }
 
-  int err = SPH_OK;
-#define ALLOC(p, n) do { if (err == SPH_OK && !cuda_ok(cudaMalloc((void**)&(p), (n) * sizeof(double)))) err = SPH_ERR_NOMEM; } while (0)
-  ALLOC(c->metric, nmet);
-  ALLOC(c->bg, 2 * (size_t)(nr + 2));
-  for (int f = 0; f < 5; f++) {
-    ALLOC(c->U[0][f], c->nf[f]); ALLOC(c->U[1][f], c->nf[f]); ALLOC(c->Ub[f], c->nf[f]);
-    ALLOC(c->R[f], c->nf[f]); ALLOC(c->X1[f], c->nf[f]); ALLOC(c->src[f], c->nf[f]);
-  }
-  ALLOC(c->coef, 13 * (size_t)c->N);
-  // scratch: block lines 12 (21 if cyclic) per point, scalar lines 3 per point each
   size_t wblk = g.per ? 21 : 12;
   size_t nscr = (wblk + 6) * (size_t)c->N + 64;
-  ALLOC(c->scr, nscr);
-  ALLOC(c->acc, 8);
-  if (err == SPH_OK && !cuda_ok(cudaMalloc((void**)&c->flag, sizeof(int)))) err = SPH_ERR_NOMEM;
-#undef ALLOC
-  if (err != SPH_OK) { free(h); free_all(c); free(c); cudaGetLastError(); return err; }
-  if (!cuda_ok(cudaMemcpy(c->metric, h, nmet * sizeof(double), cudaMemcpyHostToDevice)) ||
-      !cuda_ok(cudaMemset(c->bg, 0, 2 * (size_t)(nr + 2) * sizeof(double))) ||
-      !cuda_ok(cudaMemset(c->flag, 0, sizeof(int))))
-    err = SPH_ERR_CUDA;
+  int mixed = c->prec == SPH_PREC_MIXED;
+  int err = bufs_alloc(c->d64, c->nmet, nr, c->nf, c->N, nscr, !mixed);
+  if (err == SPH_OK && mixed) err = bufs_alloc(c->d32, c->nmet, nr, c->nf, c->N, nscr, 1);
   for (int f = 0; f < 5 && err == SPH_OK; f++) {
+    if (!cuda_ok(cudaMalloc((void**)&c->U[0][f], c->nf[f] * sizeof(double))) ||
+        !cuda_ok(cudaMalloc((void**)&c->U[1][f], c->nf[f] * sizeof(double))) ||
+        !cuda_ok(cudaMalloc((void**)&c->src[f], c->nf[f] * sizeof(double))))
+      err = SPH_ERR_NOMEM;
+  }
+  if (err == SPH_OK && (!cuda_ok(cudaMalloc((void**)&c->bg, 2 * (size_t)(nr + 2) * sizeof(double))) ||
+                        !cuda_ok(cudaMalloc((void**)&c->acc, 8 * sizeof(double))) ||
+                        !cuda_ok(cudaMalloc((void**)&c->flag, sizeof(int)))))
+    err = SPH_ERR_NOMEM;
+  if (err != SPH_OK) { cudaGetLastError(); free_all(c); free(c); return err; }
+  if (!cuda_ok(cudaMemset(c->bg, 0, 2 * (size_t)(nr + 2) * sizeof(double))) || !cuda_ok(cudaMemset(c->flag, 0, sizeof(int))))
+    err = SPH_ERR_CUDA;
+  for (int f = 0; f < 5 && err == SPH_OK; f++)
     if (!cuda_ok(cudaMemset(c->U[0][f], 0, c->nf[f] * sizeof(double))) ||
         !cuda_ok(cudaMemset(c->U[1][f], 0, c->nf[f] * sizeof(double))))
       err = SPH_ERR_CUDA;
-  }
-  free(h);
   if (err != SPH_OK) { free_all(c); free(c); return err; }
-  double* m = c->metric;
-  g.rc = m; g.rf = m + (nr + 1); g.irc = m + 2 * (nr + 1); g.irf = m + 3 * (nr + 1);
-  double* tb = m + 4 * (nr + 1);
-  g.sc = tb; g.sf = tb + (nt + 1); g.isc = tb + 2 * (nt + 1); g.isf = tb + 3 * (nt + 1);
-  g.cc = tb + 4 * (nt + 1); g.cf = tb + 5 * (nt + 1); g.cotc = tb + 6 * (nt + 1); g.cotf = tb + 7 * (nt + 1);
-  g.bgp = c->bg; g.bgT = c->bg + (nr + 2);
-  double* q = c->coef;
-  long N = c->N;
-  Coef& cf_ = c->c;
-  cf_.Pb = q; cf_.Tb = q + N; cf_.rho = q + 2 * N; cf_.beta = q + 3 * N; cf_.uc0 = q + 4 * N; cf_.uc1 = q + 5 * N;
-  cf_.uc2 = q + 6 * N; cf_.grr = q + 7 * N; cf_.gtt = q + 8 * N; cf_.gpp = q + 9 * N; cf_.srt = q + 10 * N;
-  cf_.srp = q + 11 * N; cf_.stp = q + 12 * N;
+  set_geo_ptrs(c->d64, g, c->bg, nr, nt);
+  if (mixed) set_geo_ptrs(c->d32, g, c->bg, nr, nt);
+  // zero background
+  double* zb = (double*)calloc(nr + 2, sizeof(double));
+  double* tb = (double*)calloc(nr + 2, sizeof(double));
+  err = (zb && tb) ? upload_background(c, zb, tb) : SPH_ERR_NOMEM;
+  free(zb); free(tb);
+  if (err != SPH_OK) { free_all(c); free(c); return err; }
   c->cur = 0;
   *out = c;
   return SPH_OK;
@@ -785,16 +937,20 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
 
 extern "C" int sph_set_background(sph_ctx* c, const double* p_ref, const double* T_ref) {
   if (!c) return SPH_ERR_ARG;
-  size_t n = c->g.nr + 2;
-  cudaError_t e = cudaSuccess;
-  if (p_ref) e = cudaMemcpyAsync(c->bg, p_ref, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
-  else e = cudaMemsetAsync(c->bg, 0, n * sizeof(double), c->st);
-  if (e == cudaSuccess) {
-    if (T_ref) e = cudaMemcpyAsync(c->bg + n, T_ref, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
-    else e = cudaMemsetAsync(c->bg + n, 0, n * sizeof(double), c->st);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-  return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+  size_t n = c->d64.g.nr + 2;
+  double* hp_ = (double*)calloc(n, sizeof(double));
+  double* hT = (double*)calloc(n, sizeof(double));
+  if (!hp_ || !hT) { free(hp_); free(hT); return SPH_ERR_NOMEM; }
+  if (p_ref) memcpy(hp_, p_ref, n * sizeof(double));
+  if (T_ref) memcpy(hT, T_ref, n * sizeof(double));
+  int e = SPH_OK;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess ||
+      cudaMemcpy(c->bg, hp_, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->bg + n, hT, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    e = SPH_ERR_CUDA;
+  if (e == SPH_OK) e = upload_background(c, hp_, hT);
+  free(hp_); free(hT);
+  return e;
 }
 
 static int copy_fields(sph_ctx* c, double* const* dst, const double* const* src, int kind) {
@@ -830,8 +986,8 @@ extern "C" int sph_set_iterate(sph_ctx* c, const double* const* fields, int on_d
   return e;
 }
 
-static CF cf_of(double* const* p) { CF r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
-static MF mf_of(double* const* p) { MF r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
+template <typename R> static CF<R> cf_of(R* const* p) { CF<R> r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
+template <typename R> static MF<R> mf_of(R* const* p) { MF<R> r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
 
 // bracket a launch: start event before, stop event after (when timing is on)
 static void k_begin(sph_ctx* c, int kind) {
@@ -883,35 +1039,41 @@ extern "C" int sph_profile_read(sph_ctx* c, double* ms, long long* count) {
   return SPH_OK;
 }
 
-// Ubar into c->Ub (or U^n itself when the iterate equals U^n); coefficients
-static int prepare(sph_ctx* c, int have_iter, CF* ub_out) {
+static int grid_stride_blocks(long n) {
+  long b = (n + 255) / 256;
+  return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+// Ubar into the bulk buffer (FP64 mode at k = 0: U^n itself); coefficients
+template <typename R>
+static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
   double** un = c->U[c->cur];
-  double** uk = c->U[1 - c->cur];
-  CF ub;
-  if (have_iter) {
+  double** uk = have_iter ? c->U[1 - c->cur] : un;
+  CF<R> ub;
+  if (sizeof(R) == sizeof(double) && !have_iter) {
+    for (int f = 0; f < 5; f++) ub.f[f] = (const R*)un[f];
+  } else {
     for (int f = 0; f < 5; f++) {
       long n = (long)c->nf[f];
-      int blocks = (int)((n + 255) / 256);
-      if (blocks > 152 * 16) blocks = 152 * 16;
       k_begin(c, SPH_K_AVG);
-      k_avg<<<blocks, 256, 0, c->st>>>(n, un[f], uk[f], c->Ub[f]);
+      k_avg<R><<<grid_stride_blocks(n), 256, 0, c->st>>>(n, un[f], uk[f], b.Ub[f]);
       if (launch_ok(c)) return SPH_ERR_CUDA;
     }
-    ub = cf_of(c->Ub);
-  } else {
-    ub = cf_of(un);
+    ub = cf_of(b.Ub);
   }
   k_begin(c, SPH_K_COEF);
-  k_coef<<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(c->g, c->P, ub, c->c);
+  k_coef<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->P, ub, b.c);
   if (launch_ok(c)) return SPH_ERR_CUDA;
   *ub_out = ub;
   return SPH_OK;
 }
 
-static int run_rhs(sph_ctx* c, CF ub, CF uk, double tau, CF src, int has_src, MF R) {
-  CF un = cf_of(c->U[c->cur]);
+template <typename R>
+static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, double tau, CF<double> src, int has_src, MF<R> Rout) {
+  CF<double> un = cf_of(c->U[c->cur]);
   k_begin(c, SPH_K_RHS);
-  k_rhs<<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(c->g, c->P, c->c, ub, un, uk, src, has_src, tau, R);
+  k_rhs<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, un, uk, src, has_src, tau,
+                                                                Rout);
   return launch_ok(c);
 }
 
@@ -919,8 +1081,8 @@ static int run_rhs(sph_ctx* c, CF ub, CF uk, double tau, CF src, int has_src, MF
 // the two transverse velocity components on their interior faces.  Half-open
 // ranges [a_lo, a_hi) x [b_lo, b_hi); (a, b) = (j, k) for d = r, (i, k) for
 // theta, (i, j) for phi.
-static void line_layout(const sph_ctx* c, int d, SweepArgs& S) {
-  const Geo& g = c->g;
+template <typename R>
+static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
   int nr = g.nr, nt = g.nt, np = g.np, k0 = g.per ? 0 : 1;
   int n = d == 0 ? nr : d == 1 ? nt : np;
   int lo_a[3], hi_a[3], lo_b[3], hi_b[3];
@@ -948,19 +1110,21 @@ static void line_layout(const sph_ctx* c, int d, SweepArgs& S) {
   }
 }
 
-static int run_sweep(sph_ctx* c, int d, double tau, CF ub, CF rhs, MF x, int update, CF base, MF uk) {
-  SweepArgs S;
+template <typename R>
+static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> rhs, MF<R> x, int update,
+                     CF<double> base, MF<double> uk) {
+  SweepArgs<R> S;
   memset(&S, 0, sizeof S);
-  S.g = c->g; S.P = c->P; S.c = c->c; S.ub = ub; S.d = d; S.h = 0.5 * tau;
+  S.g = b.g; S.P = c->P; S.c = b.c; S.ub = ub; S.d = d; S.h = (R)(0.5 * tau);
   S.rhs = rhs; S.x = x; S.update = update; S.base = base; S.uk = uk;
-  S.scr = c->scr; S.acc = c->acc; S.flag = c->flag;
-  line_layout(c, d, S);
+  S.scr = b.scr; S.acc = c->acc; S.flag = c->flag;
+  line_layout(c->d64.g, d, S);
   long mx = S.nl[0];
   if (S.nl[1] > mx) mx = S.nl[1];
   if (S.nl[2] > mx) mx = S.nl[2];
   dim3 grid((unsigned)((mx + 127) / 128), 3);
   k_begin(c, SPH_K_SWEEP_R + d);
-  k_sweep<<<grid, 128, 0, c->st>>>(S);
+  k_sweep<R><<<grid, 128, 0, c->st>>>(S);
   return launch_ok(c);
 }
 
@@ -970,7 +1134,7 @@ static int read_flag(sph_ctx* c, int* flag) {
   return SPH_OK;
 }
 
-static int stage_source(sph_ctx* c, const double* const* source, int on_device, CF* out) {
+static int stage_source(sph_ctx* c, const double* const* source, int on_device, CF<double>* out) {
   if (!source) { *out = cf_of(c->src); return 0; }
   if (on_device) {
     for (int f = 0; f < 5; f++) out->f[f] = source[f];
@@ -983,52 +1147,102 @@ static int stage_source(sph_ctx* c, const double* const* source, int on_device, 
   return 1;
 }
 
-extern "C" int sph_rhs(sph_ctx* c, double dt, const double* const* source, int on_device, double* const* R_out) {
-  if (!c || !R_out || !(dt > 0)) return SPH_ERR_ARG;
-  CF src;
-  int has = stage_source(c, source, on_device, &src);
-  if (has < 0) return SPH_ERR_CUDA;
-  CF ub;
-  int e = prepare(c, c->iterate_set, &ub);
-  if (e) return e;
-  CF uk = cf_of(c->iterate_set ? c->U[1 - c->cur] : c->U[c->cur]);
-  return run_rhs(c, ub, uk, dt, src, has, mf_of(R_out));
+template <typename R>
+static int convert_out(sph_ctx* c, R* const* in, double* const* out) {
+  for (int f = 0; f < 5; f++) {
+    long n = (long)c->nf[f];
+    k_cvt<R><<<grid_stride_blocks(n), 256, 0, c->st>>>(n, in[f], out[f]);
+    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
+  }
+  return SPH_OK;
 }
 
-extern "C" int sph_sweep(sph_ctx* c, int dir, double dt, const double* const* rhs, double* const* x) {
-  if (!c || !rhs || !x || dir < 0 || dir > 2 || !(dt > 0)) return SPH_ERR_ARG;
-  CF ub;
-  int e = prepare(c, c->iterate_set, &ub);
+template <typename R>
+static int convert_in(sph_ctx* c, const double* const* in, R* const* out) {
+  for (int f = 0; f < 5; f++) {
+    long n = (long)c->nf[f];
+    k_cvt_in<R><<<grid_stride_blocks(n), 256, 0, c->st>>>(n, in[f], out[f]);
+    if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
+  }
+  return SPH_OK;
+}
+
+template <typename R>
+static int rhs_impl(sph_ctx* c, Bufs<R>& b, double dt, CF<double> src, int has, double* const* R_out) {
+  CF<R> ub;
+  int e = prepare(c, b, c->iterate_set, &ub);
+  if (e) return e;
+  CF<double> uk = cf_of(c->iterate_set ? c->U[1 - c->cur] : c->U[c->cur]);
+  if (sizeof(R) == sizeof(double)) return run_rhs(c, b, ub, uk, dt, src, has, mf_of((R* const*)R_out));
+  e = run_rhs(c, b, ub, uk, dt, src, has, mf_of(b.Rb));
+  if (e) return e;
+  return convert_out(c, b.Rb, R_out);
+}
+
+extern "C" int sph_rhs(sph_ctx* c, double dt, const double* const* source, int on_device, double* const* R_out) {
+  if (!c || !R_out || !(dt > 0)) return SPH_ERR_ARG;
+  CF<double> src;
+  int has = stage_source(c, source, on_device, &src);
+  if (has < 0) return SPH_ERR_CUDA;
+  if (c->prec == SPH_PREC_MIXED) return rhs_impl(c, c->d32, dt, src, has, R_out);
+  return rhs_impl(c, c->d64, dt, src, has, R_out);
+}
+
+template <typename R>
+static int sweep_impl(sph_ctx* c, Bufs<R>& b, int dir, double dt, const double* const* rhs, double* const* x) {
+  CF<R> ub;
+  int e = prepare(c, b, c->iterate_set, &ub);
   if (e) return e;
   if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->st) != cudaSuccess) return SPH_ERR_CUDA;
-  e = run_sweep(c, dir, dt, ub, cf_of((double* const*)rhs), mf_of(x), 0, cf_of(c->U[c->cur]), mf_of(x));
+  CF<double> base = cf_of(c->U[c->cur]);
+  MF<double> ukm = mf_of(c->U[1 - c->cur]);
+  if (sizeof(R) == sizeof(double)) {
+    e = run_sweep(c, b, dir, dt, ub, cf_of((R* const*)rhs), mf_of((R* const*)x), 0, base, ukm);
+  } else {
+    e = convert_in(c, rhs, b.Rb);
+    if (!e) e = run_sweep(c, b, dir, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, base, ukm);
+    if (!e) e = convert_out(c, b.X1, x);
+  }
   if (e) return e;
   int flag = 0;
   if ((e = read_flag(c, &flag))) return e;
   return (flag & FLAG_SINGULAR) ? SPH_ERR_SINGULAR : SPH_OK;
 }
 
-extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* source, int on_device,
-                        double* residual_out) {
-  if (!c || !(dt > 0) || n_iter < 1) return SPH_ERR_ARG;
-  CF src;
-  int has = stage_source(c, source, on_device, &src);
-  if (has < 0) return SPH_ERR_CUDA;
-  if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->st) != cudaSuccess) return SPH_ERR_CUDA;
+extern "C" int sph_sweep(sph_ctx* c, int dir, double dt, const double* const* rhs, double* const* x) {
+  if (!c || !rhs || !x || dir < 0 || dir > 2 || !(dt > 0)) return SPH_ERR_ARG;
+  if (c->prec == SPH_PREC_MIXED) return sweep_impl(c, c->d32, dir, dt, rhs, x);
+  return sweep_impl(c, c->d64, dir, dt, rhs, x);
+}
+
+template <typename R>
+static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> src, int has) {
   double** un = c->U[c->cur];
   double** uk = c->U[1 - c->cur];
   int e = SPH_OK;
   for (int it = 0; it < n_iter && !e; it++) {
-    CF ub;
-    e = prepare(c, it > 0, &ub);
+    CF<R> ub;
+    e = prepare(c, b, it > 0, &ub);
     if (e) break;
-    CF ukin = cf_of(it == 0 ? un : uk);
-    e = run_rhs(c, ub, ukin, dt, src, has, mf_of(c->R));
-    if (!e) e = run_sweep(c, 0, dt, ub, cf_of(c->R), mf_of(c->X1), 0, ukin, mf_of(uk));
-    if (!e) e = run_sweep(c, 1, dt, ub, cf_of(c->X1), mf_of(c->R), 0, ukin, mf_of(uk));
+    CF<double> ukin = cf_of(it == 0 ? un : uk);
+    e = run_rhs(c, b, ub, ukin, dt, src, has, mf_of(b.Rb));
+    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, ukin, mf_of(uk));
+    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, ukin, mf_of(uk));
     if (!e && it == n_iter - 1 && cudaMemsetAsync(c->acc, 0, 5 * sizeof(double), c->st) != cudaSuccess) e = SPH_ERR_CUDA;
-    if (!e) e = run_sweep(c, 2, dt, ub, cf_of(c->R), mf_of(c->X1), 1, ukin, mf_of(uk));
+    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(b.X1), 1, ukin, mf_of(uk));
   }
+  return e;
+}
+
+extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* source, int on_device,
+                        double* residual_out) {
+  if (!c || !(dt > 0) || n_iter < 1) return SPH_ERR_ARG;
+  CF<double> src;
+  int has = stage_source(c, source, on_device, &src);
+  if (has < 0) return SPH_ERR_CUDA;
+  if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->st) != cudaSuccess) return SPH_ERR_CUDA;
+  int e = c->prec == SPH_PREC_MIXED ? step_impl(c, c->d32, dt, n_iter, src, has)
+                                    : step_impl(c, c->d64, dt, n_iter, src, has);
   if (e) return e;
   int flag = 0;
   if ((e = read_flag(c, &flag))) return e;

@@ -1,0 +1,120 @@
+"""Mixed precision (SPH_PREC_MIXED: FP32 stencils and line solves, FP64 state,
+update, divergence and cyclic corrections) against the FP64 oracle and the
+FP64 library path.
+
+Bounds:
+* each FP32 line solve: 1e-5 relative (max norm per field) against the oracle;
+* the right-hand side: 1e-5 relative per field against the oracle, plus the
+  oracle's own evaluation-order noise;
+* whole steps: the relative L2 error of the physical fields -- pressure p,
+  density rho, potential temperature theta, temperature T and velocity u -- is
+  at most 1e-6 against the FP64 path (the error statement of the mixed mode).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2004_13887_gb300 as sph
+from inputs import cases
+from tests.gpu_helpers import perturbed, rel_err, solver_for, to_dev, to_host
+from tests.test_gpu_parity import CASES, rhs_midpoint
+
+pytestmark = pytest.mark.gpu
+MIXED = sph.SPH_PREC_MIXED
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    sph.build()
+    oracle.build()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_mixed_sweep_vs_oracle(name, d):
+    g, par, bg, Un, Uk, S, dt = CASES[name]()
+    s = solver_for(g, par, bg, Un, precision=MIXED)
+    s.set_iterate(Uk)
+    rhs = perturbed(g.zeros(), [1.0] * 5, 20 + d, g)
+    x = to_host(s.sweep(d, dt, to_dev(rhs)))
+    ref = oracle.sweep(g, par, Un, Uk, dt, d, rhs, bg=bg)
+    for q in range(5):
+        assert rel_err(x[q], ref[q]) <= 1e-5, (name, d, q, rel_err(x[q], ref[q]))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_rhs_vs_oracle(name):
+    g, par, bg, Un, Uk, S, dt = CASES[name]()
+    s = solver_for(g, par, bg, Un, precision=MIXED)
+    s.set_iterate(Uk)
+    R = to_host(s.rhs(dt, S))
+    ref = oracle.rhs(g, par, Un, Uk, dt, bg=bg, S=S)
+    mid = rhs_midpoint(g, par, bg, Un, Uk, dt, S)
+    for q in range(5):
+        noise = float(np.max(np.abs(mid[q] - ref[q])))
+        err = float(np.max(np.abs(R[q] - ref[q])))
+        assert err <= 1e-5 * float(np.max(np.abs(ref[q]))) + 2 * noise, (name, q, err)
+
+
+def physical_fields(U, bg, par):
+    """p, rho, theta, T and |u| components from a state (perturbations + background)."""
+    p = U[0] + bg[0][1:-1][:, None, None]
+    T = U[4] + bg[1][1:-1][:, None, None]
+    Rg = par.cv * (par.gamma - 1.0)
+    rho = (p + par.pinf) / (Rg * T)
+    cp = par.gamma * par.cv
+    p00 = float(bg[0][1]) if float(bg[0][1]) > 0 else 1.0
+    theta = T * (p00 / p) ** (Rg / cp)
+    return {"p": p, "rho": rho, "theta": theta, "T": T, "ur": U[1], "ut": U[2], "up": U[3]}
+
+
+def l2_rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def velocity_l2(A, B):
+    num = sum(np.linalg.norm(A[k] - B[k]) ** 2 for k in ("ur", "ut", "up"))
+    den = sum(np.linalg.norm(B[k]) ** 2 for k in ("ur", "ut", "up"))
+    return math.sqrt(num / max(den, 1e-300))
+
+
+def run_both(case, nsteps, K=2, source=None):
+    s64 = solver_for(case.grid, case.par, case.bg, case.init)
+    s32 = solver_for(case.grid, case.par, case.bg, case.init, precision=MIXED)
+    for n in range(nsteps):
+        S = source((n + 0.5) * case.dt) if source else None
+        s64.step(case.dt, K, S)
+        s32.step(case.dt, K, S)
+    return to_host(s64.get_state()), to_host(s32.get_state())
+
+
+def test_mixed_steps_bubble_small():
+    c = cases.bubble((24, 32, 32), seed=1, dt=1.0)
+    U64, U32 = run_both(c, 10)
+    A, B = physical_fields(U32, c.bg, c.par), physical_fields(U64, c.bg, c.par)
+    for k in ("p", "rho", "theta", "T"):
+        assert l2_rel(A[k], B[k]) <= 1e-6, (k, l2_rel(A[k], B[k]))
+    assert velocity_l2(A, B) <= 1e-6, velocity_l2(A, B)
+
+
+def test_mixed_steps_sector_mms():
+    c = cases.sector_mms((32, 32, 32))
+    U64, U32 = run_both(c, 10, source=c.source)
+    A, B = physical_fields(U32, c.bg, c.par), physical_fields(U64, c.bg, c.par)
+    for k in ("p", "rho", "T"):
+        assert l2_rel(A[k], B[k]) <= 1e-6, (k, l2_rel(A[k], B[k]))
+    assert velocity_l2(A, B) <= 1e-6, velocity_l2(A, B)
+
+
+def test_mixed_steps_full_size_bubble():
+    """The benchmark workload, 20 steps: mixed vs FP64 per physical field."""
+    c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
+    U64, U32 = run_both(c, 20)
+    A, B = physical_fields(U32, c.bg, c.par), physical_fields(U64, c.bg, c.par)
+    errs = {k: l2_rel(A[k], B[k]) for k in ("p", "rho", "theta", "T")}
+    errs["u"] = velocity_l2(A, B)
+    print("mixed vs fp64, 20 steps:", errs)
+    for k, v in errs.items():
+        assert v <= 1e-6, (k, v)
