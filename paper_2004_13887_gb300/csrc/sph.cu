@@ -60,10 +60,10 @@ __global__ void k_cvt_in(long n, const double* __restrict__ a, R* __restrict__ o
 
 template <typename R>
 __global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
-  long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long N = (long)g.nr * g.nt * g.np;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int N = g.nr * g.nt * g.np;
   if (t >= N) return;
-  int k = (int)(t % g.np), j = (int)((t / g.np) % g.nt), i = (int)(t / ((long)g.np * g.nt));
+  int k = t % g.np, j = (t / g.np) % g.nt, i = t / (g.np * g.nt);
   const R *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
   // thermodynamics in FP64 from background + perturbation
   double pref = g.bgp[i + 1] + P.pinf, Tref = g.bgT[i + 1];
@@ -95,10 +95,10 @@ __global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
 __device__ __forceinline__ double div_ubar(const Geo<double>& g, const CF<double>& un, const CF<double>& uk, int i,
                                            int j, int k) {
   const double *ur0 = un.f[1], *ur1 = uk.f[1], *ut0 = un.f[2], *ut1 = uk.f[2], *up0 = un.f[3], *up1 = uk.f[3];
-  long a0 = IRf(g, i, j, k), a1 = IRf(g, i + 1, j, k);
-  long b0 = ITf(g, i, j, k), b1 = ITf(g, i, j + 1, k);
+  int a0 = IRf(g, i, j, k), a1 = IRf(g, i + 1, j, k);
+  int b0 = ITf(g, i, j, k), b1 = ITf(g, i, j + 1, k);
   int kp = g.per ? wrapk(g, k + 1) : k + 1;
-  long c0 = IPf(g, i, j, k), c1 = IPf(g, i, j, kp);
+  int c0 = IPf(g, i, j, k), c1 = IPf(g, i, j, kp);
   double ir = g.irc[i], is = g.isc[j];
   double f0 = g.rf[i] * g.rf[i], f1 = g.rf[i + 1] * g.rf[i + 1];
   double dr_ = (f1 * (ur0[a1] + ur1[a1]) - f0 * (ur0[a0] + ur1[a0])) * ir * ir * g.idr;
@@ -107,113 +107,116 @@ __device__ __forceinline__ double div_ubar(const Geo<double>& g, const CF<double
   return 0.5 * (dr_ + dt_ + dp_);
 }
 
-// N(Ubar) rows and R = -(U^k - U^n) - tau (N + G - S); one thread per centre
-// also owns the lower r-, theta- and phi-faces of its cell.
+// R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per centre.
 template <typename R>
-__global__ void k_rhs(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<double> un, CF<double> uk,
-                      CF<double> src, int has_src, double tau, MF<R> Rout) {
-  long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  long N = (long)g.nr * g.nt * g.np;
+__global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<double> un,
+                                               CF<double> uk, CF<double> src, int has_src, double tau, MF<R> Rout) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int N = g.nr * g.nt * g.np;
   if (t >= N) return;
-  int k = (int)(t % g.np), j = (int)((t / g.np) % g.nt), i = (int)(t / ((long)g.np * g.nt));
+  int k = t % g.np, j = (t / g.np) % g.nt, i = t / (g.np * g.nt);
   const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
-  R mu = (R)P.mu, gm = (R)P.gamma, om = (R)P.omega, h = R(0.5);
-  R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
-
-  // ---- p- and T-rows at the centre
-  {
-    R accp = R(0), accT = R(0);
-    R ap = R(0), aT = R(0);
-    for (int d = 0; d < 3; d++) {
-      int di = d == 0, dj = d == 1, dk = d == 2;
-      R pv[3], Tv[3], uv[2];
-      for (int s = -1; s <= 1; s++) {
-        pv[s + 1] = cpert(g, Pp, i + s * di, j + s * dj, k + s * dk);
-        Tv[s + 1] = cpert(g, TT, i + s * di, j + s * dj, k + s * dk);
-      }
-      if (d == 0) { uv[0] = UR[IRf(g, i, j, k)]; uv[1] = UR[IRf(g, i + 1, j, k)]; }
-      else if (d == 1) { uv[0] = UT[ITf(g, i, j, k)]; uv[1] = UT[ITf(g, i, j + 1, k)]; }
-      else { uv[0] = vp(g, UP, i, j, k); uv[1] = vp(g, UP, i, j, k + 1); }
-      RowC<R> w;
-      row_c(g, P, c, d, 0, i, j, k, w);
-      accp += w.wp[0] * pv[0] + w.wp[2] * pv[2] + w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2]
-            + w.wv[0] * uv[0] + w.wv[1] * uv[1];
-      if (d == 0) accp += w.adv * g.dbgp[i] - w.dif * g.lapT[i];
-      ap = w.a;
-      row_c(g, P, c, d, 1, i, j, k, w);
-      accT += w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2] + w.wv[0] * uv[0] + w.wv[1] * uv[1];
-      if (d == 0) accT += w.adv * g.dbgT[i] - w.dif * g.lapT[i];
-      aT = w.a;
+  R mu = (R)P.mu, gm = (R)P.gamma, h = R(0.5);
+  R ir = g.irc[i], is = g.isc[j];
+  R accp = R(0), accT = R(0);
+  R ap = R(0), aT = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    int di = d == 0, dj = d == 1, dk = d == 2;
+    R pv[3], Tv[3], uv[2];
+#pragma unroll
+    for (int s = -1; s <= 1; s++) {
+      pv[s + 1] = cpert(g, Pp, i + s * di, j + s * dj, k + s * dk);
+      Tv[s + 1] = cpert(g, TT, i + s * di, j + s * dj, k + s * dk);
     }
-    double divu = div_ubar(gd, un, uk, i, j, k);
-    R xrt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr
-          + (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth;
-    R xrp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr
-          + (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * h * ir * is * g.idph;
-    R xtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * h * ir * g.idth
-          + (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * h * ir * is * g.idph;
-    R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
-    accp += -mu * (gm - R(1)) * cross;
-    accT += -mu * c.beta[t] * cross;
-    double Np = (double)ap * divu + (double)accp, NT = (double)aT * divu + (double)accT;
-    double sp = has_src ? src.f[0][t] : 0.0, sT = has_src ? src.f[4][t] : 0.0;
-    Rout.f[0][t] = (R)(-(uk.f[0][t] - un.f[0][t]) - tau * (Np - sp));
-    Rout.f[4][t] = (R)(-(uk.f[4][t] - un.f[4][t]) - tau * (NT - sT));
+    if (d == 0) { uv[0] = UR[IRf(g, i, j, k)]; uv[1] = UR[IRf(g, i + 1, j, k)]; }
+    else if (d == 1) { uv[0] = UT[ITf(g, i, j, k)]; uv[1] = UT[ITf(g, i, j + 1, k)]; }
+    else { uv[0] = vp(g, UP, i, j, k); uv[1] = vp(g, UP, i, j, k + 1); }
+    RowC<R> w;
+    row_c(g, P, c, d, 0, i, j, k, w);
+    accp += w.wp[0] * pv[0] + w.wp[2] * pv[2] + w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2]
+          + w.wv[0] * uv[0] + w.wv[1] * uv[1];
+    if (d == 0) accp += w.adv * g.dbgp[i] - w.dif * g.lapT[i];
+    ap = w.a;
+    row_c(g, P, c, d, 1, i, j, k, w);
+    accT += w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2] + w.wv[0] * uv[0] + w.wv[1] * uv[1];
+    if (d == 0) accT += w.adv * g.dbgT[i] - w.dif * g.lapT[i];
+    aT = w.a;
   }
+  double divu = div_ubar(gd, un, uk, i, j, k);
+  R xrt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr
+        + (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth;
+  R xrp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr
+        + (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * h * ir * is * g.idph;
+  R xtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * h * ir * g.idth
+        + (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * h * ir * is * g.idph;
+  R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
+  accp += -mu * (gm - R(1)) * cross;
+  accT += -mu * c.beta[t] * cross;
+  double Np = (double)ap * divu + (double)accp, NT = (double)aT * divu + (double)accT;
+  double sp = has_src ? src.f[0][t] : 0.0, sT = has_src ? src.f[4][t] : 0.0;
+  Rout.f[0][t] = (R)(-(uk.f[0][t] - un.f[0][t]) - tau * (Np - sp));
+  Rout.f[4][t] = (R)(-(uk.f[4][t] - un.f[4][t]) - tau * (NT - sT));
+}
 
-  // ---- r-momentum on r-face i (interior faces 1..nr-1)
-  if (i >= 1) {
-    long id = IRf(g, i, j, k);
-    R wp[2], wu[3], w[3];
+// R for the momentum row of component D on its faces: one thread per face
+// (zero on wall faces, which are not unknowns).
+template <typename R, int D>
+__global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<double> un, CF<double> uk,
+                                               CF<double> src, int has_src, double tau, MF<R> Rout) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int ni = g.nr + (D == 0), nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
+  if (t >= ni * nj * nk) return;
+  int k = t % nk, j = (t / nk) % nj, i = t / (nk * nj);
+  bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
+  if (wall) { Rout.f[1 + D][t] = R(0); return; }
+  const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
+  R mu = (R)P.mu, om = (R)P.omega, h = R(0.5);
+  R wp[2], wu[3], w[3];
+  R acc;
+  if (D == 0) {
     row_f(g, P, c, UR, 0, i, j, k, wp, wu);
-    R acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i - 1, j, k))
-          + wu[0] * UR[IRf(g, i - 1, j, k)] + wu[1] * UR[id] + wu[2] * UR[IRf(g, i + 1, j, k)];
+    acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i - 1, j, k))
+        + wu[0] * UR[IRf(g, i - 1, j, k)] + wu[1] * UR[t] + wu[2] * UR[IRf(g, i + 1, j, k)];
     row_s(g, P, c, ub, 0, 1, i, j, k, w);
-    acc += w[0] * vr(g, UR, i, j - 1, k) + w[1] * UR[id] + w[2] * vr(g, UR, i, j + 1, k);
+    acc += w[0] * vr(g, UR, i, j - 1, k) + w[1] * UR[t] + w[2] * vr(g, UR, i, j + 1, k);
     row_s(g, P, c, ub, 0, 2, i, j, k, w);
-    acc += w[0] * vr(g, UR, i, j, k - 1) + w[1] * UR[id] + w[2] * vr(g, UR, i, j, k + 1);
+    acc += w[0] * vr(g, UR, i, j, k - 1) + w[1] * UR[t] + w[2] * vr(g, UR, i, j, k + 1);
     // hydrostatic part: (1/rho_f) d p_ref/dr + g = (1 - b) e + g b, b = 1 - rho_ref,f / rho_f
-    long c0 = IC(g, i - 1, j, k), c1 = IC(g, i, j, k);
-    R bf = (c.drho[c0] + c.drho[c1]) / (c.rho[c0] + c.rho[c1]);
-    R e = g.ehyd[i];
-    acc += (R(1) - bf) * e + (R)P.g * bf;
+    int c0 = IC(g, i - 1, j, k), c1 = IC(g, i, j, k);
+    R rs = c.rho[c0] + c.rho[c1];
+    R bf = sdiv(c.drho[c0] + c.drho[c1], rs);
+    acc += (R(1) - bf) * g.ehyd[i] + (R)P.g * bf;
     // D_M
-    R irf = g.irf[i], s = g.sc[j];
-    R irh = R(2) / (c.rho[c0] + c.rho[c1]);
+    R irf = g.irf[i], s = g.sc[j], is = g.isc[j];
+    R irh = sdiv(R(2), rs);
     R utf = h * (ht(g, UT, i - 1, j, k) + ht(g, UT, i, j, k));
     R upf = h * (hp(g, UP, i - 1, j, k) + hp(g, UP, i, j, k));
     R Q[2];
+#pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = i - 1 + q;
       Q[q] = (g.sf[j + 1] * UT[ITf(g, m, j + 1, k)] - g.sf[j] * UT[ITf(g, m, j, k)]) * g.irc[m] * is * g.idth
            + (vp(g, UP, m, j, k + 1) - vp(g, UP, m, j, k)) * g.irc[m] * is * g.idph;
     }
-    acc += -utf * utf * irf - upf * upf * irf + R(2) * mu * irh * UR[id] * irf * irf - R(2) * om * s * upf
+    acc += -utf * utf * irf - upf * upf * irf + R(2) * mu * irh * UR[t] * irf * irf - R(2) * om * s * upf
          - mu * irh * R(1.0 / 3.0) * g.idr * (Q[1] - Q[0]) + mu * irh * irf * (Q[0] + Q[1]);
-    double sv = has_src ? src.f[1][id] : 0.0;
-    Rout.f[1][id] = (R)(-(uk.f[1][id] - un.f[1][id]) - tau * ((double)acc - sv));
-  } else {
-    Rout.f[1][IRf(g, 0, j, k)] = R(0);
-  }
-  if (i == g.nr - 1) Rout.f[1][IRf(g, g.nr, j, k)] = R(0);
-
-  // ---- theta-momentum on theta-face j (interior faces 1..nt-1)
-  if (j >= 1) {
-    long id = ITf(g, i, j, k);
-    R wp[2], wu[3], w[3];
+  } else if (D == 1) {
+    R ir = g.irc[i];
     row_f(g, P, c, UT, 1, i, j, k, wp, wu);
-    R acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j - 1, k))
-          + wu[0] * UT[ITf(g, i, j - 1, k)] + wu[1] * UT[id] + wu[2] * UT[ITf(g, i, j + 1, k)];
+    acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j - 1, k))
+        + wu[0] * UT[ITf(g, i, j - 1, k)] + wu[1] * UT[t] + wu[2] * UT[ITf(g, i, j + 1, k)];
     row_s(g, P, c, ub, 1, 0, i, j, k, w);
-    acc += w[0] * vt(g, UT, i - 1, j, k) + w[1] * UT[id] + w[2] * vt(g, UT, i + 1, j, k);
+    acc += w[0] * vt(g, UT, i - 1, j, k) + w[1] * UT[t] + w[2] * vt(g, UT, i + 1, j, k);
     row_s(g, P, c, ub, 1, 2, i, j, k, w);
-    acc += w[0] * vt(g, UT, i, j, k - 1) + w[1] * UT[id] + w[2] * vt(g, UT, i, j, k + 1);
+    acc += w[0] * vt(g, UT, i, j, k - 1) + w[1] * UT[t] + w[2] * vt(g, UT, i, j, k + 1);
     R isfj = g.isf[j], cfj = g.cf[j], cotf = g.cotf[j];
-    R irh = R(2) / (rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
-    R ubt = UT[id];
+    R irh = sdiv(R(2), rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
+    R ubt = UT[t];
     R upf = h * (hp(g, UP, i, j - 1, k) + hp(g, UP, i, j, k));
     R vrf = h * (hr(g, UR, i, j - 1, k) + hr(g, UR, i, j, k));
     R Dr[2], Dp[2], dpf = R(0);
+#pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = j - 1 + q;
       Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * UR[IRf(g, i + 1, m, k)] - g.rf[i] * g.rf[i] * UR[IRf(g, i, m, k)])
@@ -226,30 +229,22 @@ __global__ void k_rhs(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<d
          - mu * irh * R(1.0 / 3.0) * ir * g.idth * ((Dr[1] - Dr[0]) + (Dp[1] - Dp[0]))
          - mu * irh * (R(2) * ir * ir * g.idth * (hr(g, UR, i, j, k) - hr(g, UR, i, j - 1, k))
                        - R(2) * cfj * ir * ir * isfj * isfj * dpf);
-    double sv = has_src ? src.f[2][id] : 0.0;
-    Rout.f[2][id] = (R)(-(uk.f[2][id] - un.f[2][id]) - tau * ((double)acc - sv));
   } else {
-    Rout.f[2][ITf(g, i, 0, k)] = R(0);
-  }
-  if (j == g.nt - 1) Rout.f[2][ITf(g, i, g.nt, k)] = R(0);
-
-  // ---- phi-momentum on phi-face k (interior faces, or every face if periodic)
-  if (k >= 1 || g.per) {
-    long id = IPf(g, i, j, k);
-    R wp[2], wu[3], w[3];
+    R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
     row_f(g, P, c, UP, 2, i, j, k, wp, wu);
-    R acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j, k - 1))
-          + wu[0] * vp(g, UP, i, j, k - 1) + wu[1] * UP[id] + wu[2] * vp(g, UP, i, j, k + 1);
+    acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j, k - 1))
+        + wu[0] * vp(g, UP, i, j, k - 1) + wu[1] * UP[t] + wu[2] * vp(g, UP, i, j, k + 1);
     row_s(g, P, c, ub, 2, 0, i, j, k, w);
-    acc += w[0] * vp(g, UP, i - 1, j, k) + w[1] * UP[id] + w[2] * vp(g, UP, i + 1, j, k);
+    acc += w[0] * vp(g, UP, i - 1, j, k) + w[1] * UP[t] + w[2] * vp(g, UP, i + 1, j, k);
     row_s(g, P, c, ub, 2, 1, i, j, k, w);
-    acc += w[0] * vp(g, UP, i, j - 1, k) + w[1] * UP[id] + w[2] * vp(g, UP, i, j + 1, k);
+    acc += w[0] * vp(g, UP, i, j - 1, k) + w[1] * UP[t] + w[2] * vp(g, UP, i, j + 1, k);
     R s = g.sc[j], cj = g.cc[j];
-    R irh = R(2) / (rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
-    R ubp = UP[id];
+    R irh = sdiv(R(2), rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
+    R ubp = UP[t];
     R vrf = h * (hr(g, UR, i, j, k - 1) + hr(g, UR, i, j, k));
     R vtf = h * (ht(g, UT, i, j, k - 1) + ht(g, UT, i, j, k));
     R Dr[2], Dt[2];
+#pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = k - 1 + q;
       Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * vr(g, UR, i + 1, j, m) - g.rf[i] * g.rf[i] * vr(g, UR, i, j, m))
@@ -260,12 +255,9 @@ __global__ void k_rhs(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<d
          - mu * irh * R(1.0 / 3.0) * ir * is * g.idph * ((Dr[1] - Dr[0]) + (Dt[1] - Dt[0]))
          - mu * irh * (R(2) * ir * ir * is * g.idph * (hr(g, UR, i, j, k) - hr(g, UR, i, j, k - 1))
                        + R(2) * cj * ir * ir * is * is * g.idph * (ht(g, UT, i, j, k) - ht(g, UT, i, j, k - 1)));
-    double sv = has_src ? src.f[3][id] : 0.0;
-    Rout.f[3][id] = (R)(-(uk.f[3][id] - un.f[3][id]) - tau * ((double)acc - sv));
-  } else {
-    Rout.f[3][IPf(g, i, j, 0)] = R(0);
   }
-  if (!g.per && k == g.np - 1) Rout.f[3][IPf(g, i, j, g.np)] = R(0);
+  double sv = has_src ? src.f[1 + D][t] : 0.0;
+  Rout.f[1 + D][t] = (R)(-(uk.f[1 + D][t] - un.f[1 + D][t]) - tau * ((double)acc - sv));
 }
 
 // ------------------------------------------------------------ line solvers
@@ -277,7 +269,7 @@ __device__ __forceinline__ bool inv3(const R* S, R* I) {
   R c02 = S[3] * S[7] - S[4] * S[6];
   R det = S[0] * c00 + S[1] * c01 + S[2] * c02;
   if (det == R(0) || !isfinite(det)) return false;
-  R id = R(1) / det;
+  R id = sdiv(R(1), det);
   I[0] = c00 * id; I[3] = c01 * id; I[6] = c02 * id;
   I[1] = (S[2] * S[7] - S[1] * S[8]) * id;
   I[4] = (S[0] * S[8] - S[2] * S[6]) * id;
@@ -296,7 +288,7 @@ __device__ __forceinline__ void line_pos(int d, int a, int b, int m, int& i, int
 }
 
 template <typename G>
-__device__ __forceinline__ long face_idx(const G& g, int d, int i, int j, int k) {
+__device__ __forceinline__ int face_idx(const G& g, int d, int i, int j, int k) {
   return d == 0 ? IRf(g, i, j, k) : d == 1 ? ITf(g, i, j, k) : IPf(g, i, j, k);
 }
 
@@ -350,8 +342,8 @@ struct SweepArgs {
   int update;             // mode 1: uk = base + x (FP64), accumulate norms
   CF<double> base; MF<double> uk;
   R* scr;                 // scratch
-  long scr_off[3];        // offsets of the three kinds
-  long nl[3];             // lines per kind
+  int scr_off[3];         // offsets of the three kinds
+  int nl[3];              // lines per kind
   int a0[3], nb[3], b0[3];
   double* acc;            // 5 sums of squares (mode 1)
   int* flag;
@@ -359,7 +351,7 @@ struct SweepArgs {
 
 // store a value of field f at flat index idx: x (mode 0) or uk = base + v (mode 1)
 template <typename R>
-__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, long idx, double v, double* ss, int* bad) {
+__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, int idx, double v, double* ss, int* bad) {
   if (!A.update) {
     A.x.f[f][idx] = (R)v;
   } else {
@@ -371,18 +363,18 @@ __device__ __forceinline__ void put(const SweepArgs<R>& A, int f, long idx, doub
 }
 // wall face of field f: x = 0, or uk = base (mode 1)
 template <typename R>
-__device__ __forceinline__ void put_wall(const SweepArgs<R>& A, int f, long idx) {
+__device__ __forceinline__ void put_wall(const SweepArgs<R>& A, int f, int idx) {
   if (!A.update) A.x.f[f][idx] = R(0);
   else A.uk.f[f][idx] = A.base.f[f][idx];
 }
 
-template <typename R>
-__device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, double* ss, int* bad) {
+template <typename R, int D>
+__device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, double* ss, int* bad) {
   const Geo<R>& g = S.g;
-  int d = S.d;
+  constexpr int d = D;
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
   int cyc = (d == 2 && g.per);
-  long nl = S.nl[0];
+  int nl = S.nl[0];
   R* scr = S.scr + S.scr_off[0];
   const int W = cyc ? 21 : 12;  // C' (9) + d' (3 per right-hand side)
   const int NR = cyc ? 4 : 1;
@@ -394,7 +386,7 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
     R A[9], B[9], C[9];
     assemble_block(g, S.P, S.c, S.ub, d, n, cyc, m, i, j, k, S.h, A, B, C);
     R rr[12];
-    long ic = IC(g, i, j, k);
+    int ic = IC(g, i, j, k);
     rr[0] = S.rhs.f[0][ic];
     rr[NR] = S.rhs.f[4][ic];
     R ru = R(0);
@@ -448,9 +440,9 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
         dp[r * NR + q] = Si[r * 3] * y[q] + Si[r * 3 + 1] * y[NR + q] + Si[r * 3 + 2] * y[2 * NR + q];
     }
     if (m < n - 1) {
-      R* s = scr + (long)m * W * nl + line;
-      for (int q = 0; q < 9; q++) s[(long)q * nl] = Cp[q];
-      for (int q = 0; q < 3 * NR; q++) s[(long)(9 + q) * nl] = dp[q];
+      R* s = scr + m * W * nl + line;
+      for (int q = 0; q < 9; q++) s[q * nl] = Cp[q];
+      for (int q = 0; q < 3 * NR; q++) s[(9 + q) * nl] = dp[q];
     }
   }
   // back substitution, all NR columns
@@ -459,10 +451,10 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
   R x0[12];
   for (int m = n - 1; m >= 0; m--) {
     if (m < n - 1) {
-      const R* s = scr + (long)m * W * nl + line;
+      const R* s = scr + m * W * nl + line;
       R C_[9], d_[12];
-      for (int q = 0; q < 9; q++) C_[q] = s[(long)q * nl];
-      for (int q = 0; q < 3 * NR; q++) d_[q] = s[(long)(9 + q) * nl];
+      for (int q = 0; q < 9; q++) C_[q] = s[q * nl];
+      for (int q = 0; q < 3 * NR; q++) d_[q] = s[(9 + q) * nl];
       R xn[12];
       for (int r = 0; r < 3; r++)
         for (int q = 0; q < NR; q++)
@@ -472,7 +464,7 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
     if (!cyc) {
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
-      long ic = IC(g, i, j, k);
+      int ic = IC(g, i, j, k);
       put(S, 0, ic, (double)xs[0], ss, bad);
       put(S, 4, ic, (double)xs[1], ss, bad);
       if (m < n - 1) {
@@ -489,16 +481,16 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
       }
     } else {
       // keep x (all columns) in the d'-slots for the Woodbury combination
-      R* s = scr + (long)m * W * nl + line;
-      for (int q = 0; q < 3 * NR; q++) s[(long)(9 + q) * nl] = xs[q];
+      R* s = scr + m * W * nl + line;
+      for (int q = 0; q < 3 * NR; q++) s[(9 + q) * nl] = xs[q];
       if (m == 0) for (int q = 0; q < 12; q++) x0[q] = xs[q];
     }
   }
   if (cyc) {
     // V^T y = y_0 + GiA y_{n-1};  V^T Z = Z_0 + GiA Z_{n-1};  f = (I + V^T Z)^{-1} V^T y  (FP64)
-    const R* sl = scr + (long)(n - 1) * W * nl + line;
+    const R* sl = scr + (n - 1) * W * nl + line;
     double xl[12], vy[3], vz[9], vi[9], fcor[3];
-    for (int q = 0; q < 12; q++) xl[q] = (double)sl[(long)(9 + q) * nl];
+    for (int q = 0; q < 12; q++) xl[q] = (double)sl[(9 + q) * nl];
     for (int r = 0; r < 3; r++) {
       vy[r] = (double)x0[r * 4] + (double)GiA[r * 3] * xl[0] + (double)GiA[r * 3 + 1] * xl[4] + (double)GiA[r * 3 + 2] * xl[8];
       for (int q = 0; q < 3; q++)
@@ -508,15 +500,15 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
     if (!inv3(vz, vi)) { *bad |= FLAG_SINGULAR; return; }
     for (int r = 0; r < 3; r++) fcor[r] = vi[r * 3] * vy[0] + vi[r * 3 + 1] * vy[1] + vi[r * 3 + 2] * vy[2];
     for (int m = 0; m < n; m++) {
-      const R* s = scr + (long)m * W * nl + line;
+      const R* s = scr + m * W * nl + line;
       double xv[3];
       for (int r = 0; r < 3; r++) {
-        xv[r] = (double)s[(long)(9 + r * 4) * nl];
-        for (int q = 0; q < 3; q++) xv[r] -= (double)s[(long)(9 + r * 4 + 1 + q) * nl] * fcor[q];
+        xv[r] = (double)s[(9 + r * 4) * nl];
+        for (int q = 0; q < 3; q++) xv[r] -= (double)s[(9 + r * 4 + 1 + q) * nl] * fcor[q];
       }
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
-      long ic = IC(g, i, j, k);
+      int ic = IC(g, i, j, k);
       put(S, 0, ic, xv[0], ss, bad);
       put(S, 4, ic, xv[1], ss, bad);
       int fk = (m + 1 == n) ? 0 : m + 1;
@@ -526,10 +518,8 @@ __device__ void block_line(const SweepArgs<R>& S, long line, int a, int b, doubl
 }
 
 // transverse component of kind 1/2 along d
-__device__ __forceinline__ int trans_comp(int d, int kind) {
-  if (d == 0) return kind == 1 ? 1 : 2;
-  if (d == 1) return kind == 1 ? 0 : 2;
-  return kind == 1 ? 0 : 1;
+__host__ __device__ constexpr int trans_comp(int d, int kind) {
+  return d == 0 ? (kind == 1 ? 1 : 2) : d == 1 ? (kind == 1 ? 0 : 2) : (kind == 1 ? 0 : 1);
 }
 
 // output of a transverse line value at cell m, plus the wall faces of that
@@ -554,14 +544,14 @@ __device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i,
   }
 }
 
-template <typename R>
-__device__ void scalar_line(const SweepArgs<R>& S, int kind, long line, int a, int b, double* ss, int* bad) {
+template <typename R, int D, int KIND>
+__device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, double* ss, int* bad) {
   const Geo<R>& g = S.g;
-  int d = S.d;
+  constexpr int d = D, kind = KIND;
   int cc = trans_comp(d, kind);
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
   int cyc = (d == 2 && g.per);
-  long nl = S.nl[kind];
+  int nl = S.nl[kind];
   R* scr = S.scr + S.scr_off[kind];
   const R* rhs = S.rhs.f[1 + cc];
   R cp = R(0), dy = R(0), dz = R(0);
@@ -584,10 +574,10 @@ __device__ void scalar_line(const SweepArgs<R>& S, int kind, long line, int a, i
     R r = rhs[face_idx(g, cc, i, j, k)];
     R den = bm - am * cp;
     if (den == R(0) || !isfinite(den)) { *bad |= FLAG_SINGULAR; return; }
-    R iden = R(1) / den;
+    R iden = sdiv(R(1), den);
     cp = cm * iden;
     dy = (r - am * dy) * iden;
-    R* s = scr + (long)m * 3 * nl + line;
+    R* s = scr + m * 3 * nl + line;
     s[0] = cp;
     s[nl] = dy;
     if (cyc) { dz = (zr - am * dz) * iden; s[2 * nl] = dz; }
@@ -596,7 +586,7 @@ __device__ void scalar_line(const SweepArgs<R>& S, int kind, long line, int a, i
     R xy = dy;
     for (int m = n - 1; m >= 0; m--) {
       if (m < n - 1) {
-        const R* t = scr + (long)m * 3 * nl + line;
+        const R* t = scr + m * 3 * nl + line;
         xy = t[nl] - t[0] * xy;
       }
       int i, j, k;
@@ -608,14 +598,14 @@ __device__ void scalar_line(const SweepArgs<R>& S, int kind, long line, int a, i
   // cyclic: back-substitute both columns, then combine in FP64
   R xy = dy, xz = dz, yl = dy, zl = dz;
   for (int m = n - 2; m >= 0; m--) {
-    R* t = scr + (long)m * 3 * nl + line;
+    R* t = scr + m * 3 * nl + line;
     xy = t[nl] - t[0] * xy;
     xz = t[2 * nl] - t[0] * xz;
     t[nl] = xy;
     t[2 * nl] = xz;
   }
   {
-    R* t = scr + (long)(n - 1) * 3 * nl + line;
+    R* t = scr + (n - 1) * 3 * nl + line;
     t[nl] = yl;
     t[2 * nl] = zl;
   }
@@ -623,24 +613,25 @@ __device__ void scalar_line(const SweepArgs<R>& S, int kind, long line, int a, i
   double vy = (double)xy + ag * (double)yl, vz = (double)xz + ag * (double)zl;
   double f = vy / (1.0 + vz);
   for (int m = 0; m < n; m++) {
-    const R* t = scr + (long)m * 3 * nl + line;
+    const R* t = scr + m * 3 * nl + line;
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
     scalar_put(S, cc, i, j, k, (double)t[nl] - f * (double)t[2 * nl], ss, bad);
   }
 }
 
-template <typename R>
-__global__ void k_sweep(SweepArgs<R> S) {
+template <typename R, int D>
+__global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
   int kind = blockIdx.y;
-  long line = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  int line = blockIdx.x * blockDim.x + threadIdx.x;
   double ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   if (line < S.nl[kind]) {
     int a = (int)(line / S.nb[kind]) + S.a0[kind];
     int b = (int)(line % S.nb[kind]) + S.b0[kind];
-    if (kind == 0) block_line(S, line, a, b, ss, &bad);
-    else scalar_line(S, kind, line, a, b, ss, &bad);
+    if (kind == 0) block_line<R, D>(S, line, a, b, ss, &bad);
+    else if (kind == 1) scalar_line<R, D, 1>(S, line, a, b, ss, &bad);
+    else scalar_line<R, D, 2>(S, line, a, b, ss, &bad);
   }
   if (bad) atomicOr(S.flag, bad);
   if (S.update) {
@@ -901,6 +892,10 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
 
   size_t wblk = g.per ? 21 : 12;
   size_t nscr = (wblk + 6) * (size_t)c->N + 64;
+  // kernels index with 32-bit ints: every array, and the scratch, must fit
+  if (nscr >= (size_t)2147483647 || c->nf[1] >= (size_t)2147483647 || c->nf[3] >= (size_t)2147483647) {
+    free(c->hmet); free(c); return SPH_ERR_ARG;
+  }
   int mixed = c->prec == SPH_PREC_MIXED;
   int err = bufs_alloc(c->d64, c->nmet, nr, c->nf, c->N, nscr, !mixed);
   if (err == SPH_OK && mixed) err = bufs_alloc(c->d32, c->nmet, nr, c->nf, c->N, nscr, 1);
@@ -1072,8 +1067,17 @@ template <typename R>
 static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, double tau, CF<double> src, int has_src, MF<R> Rout) {
   CF<double> un = cf_of(c->U[c->cur]);
   k_begin(c, SPH_K_RHS);
-  k_rhs<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, un, uk, src, has_src, tau,
-                                                                Rout);
+  k_rhs_c<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, un, uk, src, has_src,
+                                                                  tau, Rout);
+  if (launch_ok(c)) return SPH_ERR_CUDA;
+  k_begin(c, SPH_K_RHS);
+  k_rhs_u<R, 0><<<(unsigned)((c->nf[1] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, un, uk, src, has_src, tau, Rout);
+  if (launch_ok(c)) return SPH_ERR_CUDA;
+  k_begin(c, SPH_K_RHS);
+  k_rhs_u<R, 1><<<(unsigned)((c->nf[2] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, un, uk, src, has_src, tau, Rout);
+  if (launch_ok(c)) return SPH_ERR_CUDA;
+  k_begin(c, SPH_K_RHS);
+  k_rhs_u<R, 2><<<(unsigned)((c->nf[3] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, un, uk, src, has_src, tau, Rout);
   return launch_ok(c);
 }
 
@@ -1103,8 +1107,8 @@ static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
   for (int q = 0; q < 3; q++) {
     int na = hi_a[q] - lo_a[q], nb = hi_b[q] - lo_b[q];
     S.a0[q] = lo_a[q]; S.b0[q] = lo_b[q]; S.nb[q] = nb > 0 ? nb : 1;
-    S.nl[q] = (na > 0 && nb > 0) ? (long)na * nb : 0;
-    S.scr_off[q] = off;
+    S.nl[q] = (na > 0 && nb > 0) ? na * nb : 0;
+    S.scr_off[q] = (int)off;
     long w = q == 0 ? (g.per && d == 2 ? 21 : 12) : 3;
     off += w * (long)n * S.nl[q];
   }
@@ -1119,12 +1123,14 @@ static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> 
   S.rhs = rhs; S.x = x; S.update = update; S.base = base; S.uk = uk;
   S.scr = b.scr; S.acc = c->acc; S.flag = c->flag;
   line_layout(c->d64.g, d, S);
-  long mx = S.nl[0];
+  int mx = S.nl[0];
   if (S.nl[1] > mx) mx = S.nl[1];
   if (S.nl[2] > mx) mx = S.nl[2];
   dim3 grid((unsigned)((mx + 127) / 128), 3);
   k_begin(c, SPH_K_SWEEP_R + d);
-  k_sweep<R><<<grid, 128, 0, c->st>>>(S);
+  if (d == 0) k_sweep<R, 0><<<grid, 128, 0, c->st>>>(S);
+  else if (d == 1) k_sweep<R, 1><<<grid, 128, 0, c->st>>>(S);
+  else k_sweep<R, 2><<<grid, 128, 0, c->st>>>(S);
   return launch_ok(c);
 }
 

@@ -55,10 +55,16 @@ constexpr int NCOEF = 14;
 template <typename R> struct CF { const R* f[5]; };
 template <typename R> struct MF { R* f[5]; };
 
-template <typename G> __device__ __forceinline__ long IC(const G& g, int i, int j, int k) { return ((long)i * g.nt + j) * g.np + k; }
-template <typename G> __device__ __forceinline__ long IRf(const G& g, int i, int j, int k) { return ((long)i * g.nt + j) * g.np + k; }
-template <typename G> __device__ __forceinline__ long ITf(const G& g, int i, int j, int k) { return ((long)i * (g.nt + 1) + j) * g.np + k; }
-template <typename G> __device__ __forceinline__ long IPf(const G& g, int i, int j, int k) { return ((long)i * g.nt + j) * g.npf + k; }
+// 32-bit flat indices: the host refuses grids whose arrays (and line-solve
+// scratch) would not fit in an int.
+template <typename G> __device__ __forceinline__ int IC(const G& g, int i, int j, int k) { return (i * g.nt + j) * g.np + k; }
+template <typename G> __device__ __forceinline__ int IRf(const G& g, int i, int j, int k) { return (i * g.nt + j) * g.np + k; }
+template <typename G> __device__ __forceinline__ int ITf(const G& g, int i, int j, int k) { return (i * (g.nt + 1) + j) * g.np + k; }
+template <typename G> __device__ __forceinline__ int IPf(const G& g, int i, int j, int k) { return (i * g.nt + j) * g.npf + k; }
+
+// a / b; the mixed path uses the fast single-precision division (2 ulp)
+template <typename R> __device__ __forceinline__ R sdiv(R a, R b) { return a / b; }
+template <> __device__ __forceinline__ float sdiv<float>(float a, float b) { return __fdividef(a, b); }
 
 template <typename G> __device__ __forceinline__ int wrapk(const G& g, int k) { return k < 0 ? k + g.np : (k >= g.np ? k - g.np : k); }
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -137,7 +143,7 @@ struct RowC {
 template <typename R>
 __device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<R>& c, int d, int isT, int i, int j,
                                       int k, RowC<R>& w) {
-  long id = IC(g, i, j, k);
+  int id = IC(g, i, j, k);
   R gm = (R)P.gamma, mu = (R)P.mu;
   R be = c.beta[id];
   R alin = isT ? (gm - R(1)) * c.Tb[id] : gm * c.Pb[id];
@@ -203,7 +209,7 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
                                       int j, int k, R wp[2], R wu[3]) {
   R mu = (R)P.mu;
   if (d == 0) {
-    R irh = R(2) / (rho_at(g, c, i - 1, j, k) + rho_at(g, c, i, j, k));
+    R irh = sdiv(R(2), rho_at(g, c, i - 1, j, k) + rho_at(g, c, i, j, k));
     R irf = g.irf[i];
     wp[0] = -irh * g.idr; wp[1] = irh * g.idr;
     R adv = R(0.5) * ubd[IRf(g, i, j, k)] * g.idr;
@@ -216,7 +222,7 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
     wu[1] = -lap * (c0 + c1) - gdv * f0 * (ic1 + ic0);
     wu[2] = adv + lap * c1 + gdv * fp * ic1;
   } else if (d == 1) {
-    R irh = R(2) / (rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
+    R irh = sdiv(R(2), rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
     R ir = g.irc[i], isf = g.isf[j];
     wp[0] = -irh * ir * g.idth; wp[1] = irh * ir * g.idth;
     R adv = R(0.5) * ubd[ITf(g, i, j, k)] * ir * g.idth;
@@ -227,7 +233,7 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
     wu[1] = -lap * (c0 + c1) - gdv * g.sf[j] * (g.isc[j] + g.isc[j - 1]);
     wu[2] = adv + lap * c1 + gdv * g.sf[j + 1] * g.isc[j];
   } else {
-    R irh = R(2) / (rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
+    R irh = sdiv(R(2), rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
     R ir = g.irc[i], is = g.isc[j];
     wp[0] = -irh * ir * is * g.idph; wp[1] = irh * ir * is * g.idph;
     R adv = R(0.5) * ubd[IPf(g, i, j, k)] * ir * is * g.idph;
@@ -245,7 +251,7 @@ __device__ __forceinline__ void row_s(const Geo<R>& g, const Par& P, const Coef<
   if (cc == 0) rsum = rho_at(g, c, i - 1, j, k) + rho_at(g, c, i, j, k);
   else if (cc == 1) rsum = rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k);
   else rsum = rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k);
-  R irh = R(2) / rsum;
+  R irh = sdiv(R(2), rsum);
   R ir = cc == 0 ? g.irf[i] : g.irc[i];
   R is = cc == 1 ? g.isf[j] : g.isc[j];
   R ua;
