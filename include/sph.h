@@ -105,15 +105,30 @@ int sph_set_iterate(sph_ctx* ctx, const double* const* fields, int on_device);
 int sph_rhs(sph_ctx* ctx, double dt, const double* const* source, int source_on_device, double* const* R_out);
 int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double* const* x);
 
+/* Line solver of the sweeps in SPH_PREC_MIXED mode (eqs. spl1-spl3 leave the
+ * method of solving each line open; Section 2.2 names the block Thomas
+ * algorithm).  SPH_LINES_PARTITIONED (the default): for lines of 64, 128 or 256
+ * cells, one warp per line -- each lane eliminates a chunk of n/32 cells, the
+ * chunk-boundary unknowns are solved by parallel cyclic reduction across the
+ * warp, then each lane back-substitutes; other lengths use the block Thomas
+ * path.  SPH_LINES_THOMAS: block (and scalar) Thomas, one thread per line, with
+ * the Woodbury / Sherman-Morrison correction on cyclic lines.  Both give the
+ * exact solution up to rounding (no pivoting between blocks in either).  The
+ * FP64 mode always uses block Thomas.  Returns SPH_ERR_ARG for other values. */
+#define SPH_LINES_THOMAS 0
+#define SPH_LINES_PARTITIONED 1
+int sph_set_line_solver(sph_ctx* ctx, int which);
+
 /* Number of this library's kernel launches since creation (for accounting). */
 long long sph_launch_count(const sph_ctx* ctx);
 
 /* Per-kernel timing.  sph_profile(ctx, 1) clears the record and starts timing
- * every launch with a pair of CUDA events on the context's stream; 0 stops.
- * sph_profile_read synchronises the stream and writes, for each kernel kind
- * SPH_K_* (SPH_NKERNELS entries), the summed duration in ms and the launch
- * count (either pointer may be NULL).  At most 65536 launches are recorded;
- * later ones are counted but not timed (returned count includes them). */
+ * every kernel stage (one launch, or the one to three launches of a
+ * partitioned sweep) with a pair of CUDA events on the context's stream; 0
+ * stops.  sph_profile_read synchronises the stream and writes, for each kernel
+ * kind SPH_K_* (SPH_NKERNELS entries), the summed duration in ms and the stage
+ * count (either pointer may be NULL).  At most 65536 stages are recorded;
+ * later ones are counted but not timed (the returned count includes them). */
 #define SPH_K_AVG 0
 #define SPH_K_COEF 1
 #define SPH_K_RHS 2

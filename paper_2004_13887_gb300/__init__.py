@@ -16,10 +16,13 @@ import numpy as np
 
 from ._build import LIB, build
 
-__all__ = ["build", "load", "Solver", "SphError", "sph_field_size", "SPH_PREC_FP64", "SPH_PREC_MIXED"]
+__all__ = ["build", "load", "Solver", "SphError", "sph_field_size", "SPH_PREC_FP64", "SPH_PREC_MIXED",
+           "SPH_LINES_THOMAS", "SPH_LINES_PARTITIONED"]
 
 SPH_PREC_FP64 = 0
 SPH_PREC_MIXED = 1
+SPH_LINES_THOMAS = 0
+SPH_LINES_PARTITIONED = 1
 
 _ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "non-finite state",
            -4: "zero pivot in a line solve", -5: "device allocation failed"}
@@ -58,6 +61,7 @@ SIGNATURES = {
     "sph_set_iterate": ([_CTX, _PP, C.c_int], C.c_int),
     "sph_rhs": ([_CTX, C.c_double, _PP, C.c_int, _PP], C.c_int),
     "sph_sweep": ([_CTX, C.c_int, C.c_double, _PP, _PP], C.c_int),
+    "sph_set_line_solver": ([_CTX, C.c_int], C.c_int),
     "sph_launch_count": ([_CTX], C.c_longlong),
     "sph_profile": ([_CTX, C.c_int], C.c_int),
     "sph_profile_read": ([_CTX, _DP, C.POINTER(C.c_longlong)], C.c_int),
@@ -236,6 +240,10 @@ class Solver:
         po = _Ptrs(out, self.shapes, True)
         _check(load().sph_sweep(self._h, int(direction), float(dt), pi.arr, po.arr), "sph_sweep")
         return out
+
+    def set_line_solver(self, which: int):
+        """SPH_LINES_PARTITIONED (default) or SPH_LINES_THOMAS for the mixed-precision sweeps."""
+        _check(load().sph_set_line_solver(self._h, int(which)), "sph_set_line_solver")
 
     KERNELS = ("avg", "coef", "rhs", "sweep_r", "sweep_theta", "sweep_phi")
 

@@ -292,26 +292,27 @@ __device__ __forceinline__ int face_idx(const G& g, int d, int i, int j, int k) 
   return d == 0 ? IRf(g, i, j, k) : d == 1 ? ITf(g, i, j, k) : IPf(g, i, j, k);
 }
 
-// Assemble block m of (I + h D_d) on a line; h = tau/2.
+// Assemble block m of (I + h D_d) on a line from the loaded centre values (cq)
+// and, when the line has face m+1 (m < n-1 or cyclic), the face values fq at
+// face coordinates (fi, fj); h = tau/2.
 template <typename R>
-__device__ void assemble_block(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int d, int n, int cyc,
-                               int m, int i, int j, int k, R h, R* A, R* B, R* C) {
+__device__ __forceinline__ void assemble_pts(const Geo<R>& g, const Par& P, const CPt<R>& cq, const FPt<R>& fq, int d,
+                                             int n, int cyc, int m, int i, int j, int fi, int fj, R h, R* A, R* B,
+                                             R* C) {
   RowC<R> w;
 #pragma unroll
   for (int q = 0; q < 9; q++) { A[q] = R(0); B[q] = R(0); C[q] = R(0); }
-  row_c(g, P, c, d, 0, i, j, k, w);
+  row_cw(g, P, cq, d, 0, i, j, w);
   A[0] = h * w.wp[0]; A[1] = h * w.wT[0]; A[2] = h * (w.a * w.gd[0] + w.wv[0]);
   B[0] = h * w.wp[1]; B[1] = h * w.wT[1]; B[2] = h * (w.a * w.gd[1] + w.wv[1]);
   C[0] = h * w.wp[2]; C[1] = h * w.wT[2];
-  row_c(g, P, c, d, 1, i, j, k, w);
+  row_cw(g, P, cq, d, 1, i, j, w);
   A[4] = h * w.wT[0]; A[5] = h * (w.a * w.gd[0] + w.wv[0]);
   B[4] = h * w.wT[1]; B[5] = h * (w.a * w.gd[1] + w.wv[1]);
   C[4] = h * w.wT[2];
   if (m < n - 1 || cyc) {
-    int fi = i, fj = j, fk = k;
-    if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = (m + 1 == n) ? 0 : m + 1;
     R fp[2], fu[3];
-    row_f(g, P, c, ub.f[1 + d], d, fi, fj, fk, fp, fu);
+    row_fw(g, P, fq, d, fi, fj, fp, fu);
     A[8] = h * fu[0];
     B[6] = h * fp[0]; B[8] = h * fu[1];
     C[6] = h * fp[1]; C[8] = h * fu[2];
@@ -331,6 +332,24 @@ __device__ void assemble_block(const Geo<R>& g, const Par& P, const Coef<R>& c, 
       A[8] = R(0); B[6] = R(0); B[7] = R(0); B[8] = R(1);
     }
   }
+}
+
+// face m+1 of cell m on a line along d (wrapping to 0 on a cyclic line)
+__device__ __forceinline__ void next_face(int d, int n, int m, int i, int j, int k, int& fi, int& fj, int& fk) {
+  fi = i; fj = j; fk = k;
+  if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = (m + 1 == n) ? 0 : m + 1;
+}
+
+// Assemble block m of (I + h D_d) on a line; h = tau/2.
+template <typename R>
+__device__ void assemble_block(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int d, int n, int cyc,
+                               int m, int i, int j, int k, R h, R* A, R* B, R* C) {
+  CPt<R> cq = load_c(c, d, IC(g, i, j, k));
+  FPt<R> fq = {R(1), R(1), R(0)};
+  int fi, fj, fk;
+  next_face(d, n, m, i, j, k, fi, fj, fk);
+  if (m < n - 1 || cyc) fq = load_f(g, c, ub.f[1 + d], d, fi, fj, fk);
+  assemble_pts(g, P, cq, fq, d, n, cyc, m, i, j, fi, fj, h, A, B, C);
 }
 
 template <typename R>
@@ -643,6 +662,8 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
   }
 }
 
+#include "sph_lines.cuh"
+
 // ============================================================== host side
 
 // Device buffers of one precision.
@@ -686,6 +707,9 @@ struct sph_ctx {
   int nev, evcap;
   long long kcount[SPH_NKERNELS];
   int cur_kind;
+  int nsm;               // multiprocessors of the device
+  int line_solver;       // SPH_LINES_* for the mixed path
+  size_t nscr;           // floats in each bulk scratch buffer
 };
 
 #define PROF_CAP 65536
@@ -714,6 +738,12 @@ extern "C" const char* sph_strerror(int code) {
     case SPH_ERR_NOMEM: return "device allocation failed";
     default: return "unknown error";
   }
+}
+
+extern "C" int sph_set_line_solver(sph_ctx* ctx, int which) {
+  if (!ctx || (which != SPH_LINES_THOMAS && which != SPH_LINES_PARTITIONED)) return SPH_ERR_ARG;
+  ctx->line_solver = which;
+  return SPH_OK;
 }
 
 extern "C" long long sph_launch_count(const sph_ctx* ctx) { return ctx ? ctx->launches : 0; }
@@ -861,8 +891,10 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   sph_ctx* c = (sph_ctx*)calloc(1, sizeof(sph_ctx));
   if (!c) return SPH_ERR_NOMEM;
   cudaGetDevice(&c->dev);
+  if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || c->nsm < 1) c->nsm = 1;
   c->st = (cudaStream_t)stream;
   c->prec = pa->precision;
+  c->line_solver = SPH_LINES_PARTITIONED;
   Geo<double> g;
   memset(&g, 0, sizeof g);
   g.nr = gr->nr; g.nt = gr->nth; g.np = gr->nph; g.per = gr->periodic_phi ? 1 : 0;
@@ -892,11 +924,14 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
 
   size_t wblk = g.per ? 21 : 12;
   size_t nscr = (wblk + 6) * (size_t)c->N + 64;
+  // the partitioned solver's factor slots take up to 19.5 N floats
+  if (c->prec == SPH_PREC_MIXED && nscr < 20 * (size_t)c->N + 64) nscr = 20 * (size_t)c->N + 64;
   // kernels index with 32-bit ints: every array, and the scratch, must fit
   if (nscr >= (size_t)2147483647 || c->nf[1] >= (size_t)2147483647 || c->nf[3] >= (size_t)2147483647) {
     free(c->hmet); free(c); return SPH_ERR_ARG;
   }
   int mixed = c->prec == SPH_PREC_MIXED;
+  c->nscr = nscr;
   int err = bufs_alloc(c->d64, c->nmet, nr, c->nf, c->N, nscr, !mixed);
   if (err == SPH_OK && mixed) err = bufs_alloc(c->d32, c->nmet, nr, c->nf, c->N, nscr, 1);
   for (int f = 0; f < 5 && err == SPH_OK; f++) {
@@ -1114,6 +1149,64 @@ static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
   }
 }
 
+// Partitioned line solver (mixed path) for lines of n = 32 P cells: one
+// launch per line kind, one block per group of 32/P lines.
+template <typename K>
+static int lines_smem(K kern, size_t smem) {
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return SPH_ERR_CUDA;
+  return SPH_OK;
+}
+
+static int lines_groups(const SweepArgs<float>& S, int kind, int NW) {
+  if (S.nl[kind] <= 0) return 0;
+  int nb = S.nb[kind], na = S.nl[kind] / nb;
+  return na * ((nb + NW - 1) / NW);
+}
+
+// whether the partitioned solver can take the lines along d
+static int lines_ok(const sph_ctx* c, int d) {
+  const Geo<double>& g = c->d64.g;
+  int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
+  return n == 64 || n == 128 || n == 256;
+}
+
+template <int D, int P>
+static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
+  constexpr int NW = 32 / P, NT = 32 * NW;
+  const size_t smb = (size_t)lines::blk_fields(P) * lines::FS * sizeof(float);
+  const size_t sms = (size_t)lines::NFS * lines::FS * sizeof(float);
+  int ng, e;
+  k_begin(c, SPH_K_SWEEP_R + D);
+  if ((ng = lines_groups(S, 0, NW)) > 0) {
+    // one factor slot per block
+    if ((size_t)ng * NW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
+    if ((e = lines_smem(lines::k_lines_blk<D, P>, smb))) return e;
+    lines::k_lines_blk<D, P><<<ng, NT, smb, c->st>>>(S);
+    c->launches++;
+  }
+  if ((ng = lines_groups(S, 1, NW)) > 0) {
+    if ((e = lines_smem(lines::k_lines_sca<D, P, 1>, sms))) return e;
+    lines::k_lines_sca<D, P, 1><<<ng, NT, sms, c->st>>>(S);
+    c->launches++;
+  }
+  if ((ng = lines_groups(S, 2, NW)) > 0) {
+    if ((e = lines_smem(lines::k_lines_sca<D, P, 2>, sms))) return e;
+    lines::k_lines_sca<D, P, 2><<<ng, NT, sms, c->st>>>(S);
+    c->launches++;
+  }
+  c->launches--;  // launch_ok counts one more
+  return launch_ok(c);
+}
+
+template <int D>
+static int run_lines_d(sph_ctx* c, SweepArgs<float>& S, int n) {
+  if (n == 64) return run_lines<D, 2>(c, S);
+  if (n == 128) return run_lines<D, 4>(c, S);
+  return run_lines<D, 8>(c, S);
+}
+
 template <typename R>
 static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> rhs, MF<R> x, int update,
                      CF<double> base, MF<double> uk) {
@@ -1123,6 +1216,14 @@ static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> 
   S.rhs = rhs; S.x = x; S.update = update; S.base = base; S.uk = uk;
   S.scr = b.scr; S.acc = c->acc; S.flag = c->flag;
   line_layout(c->d64.g, d, S);
+  if (sizeof(R) == sizeof(float) && c->line_solver == SPH_LINES_PARTITIONED && lines_ok(c, d)) {
+    SweepArgs<float>& Sf = *reinterpret_cast<SweepArgs<float>*>(&S);
+    const Geo<double>& g = c->d64.g;
+    int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
+    if (d == 0) return run_lines_d<0>(c, Sf, n);
+    if (d == 1) return run_lines_d<1>(c, Sf, n);
+    return run_lines_d<2>(c, Sf, n);
+  }
   int mx = S.nl[0];
   if (S.nl[1] > mx) mx = S.nl[1];
   if (S.nl[2] > mx) mx = S.nl[2];

@@ -126,6 +126,10 @@ __device__ __forceinline__ R rho_at(const Geo<R>& g, const Coef<R>& c, int i, in
 }
 
 // ------------------------------------------------------------------- rows
+// Each row is split into a loader (the values it reads from memory) and a
+// weight function (pure arithmetic on those values and the metric tables), so
+// that the line solvers can fetch the next row while eliminating the current.
+//
 // p-row (isT = 0) or T-row (isT = 1) of D_d at centre (i,j,k).  The coupling to
 // the normal velocity u_d on faces m, m+1 is split as
 //   wu[q] = a * gd[q] + wv[q],
@@ -140,16 +144,30 @@ struct RowC {
   R dif;            // conduction coefficient: wT += -dif * geometric Laplacian
 };
 
+// centre coefficients the p- and T-rows of direction d read
 template <typename R>
-__device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<R>& c, int d, int isT, int i, int j,
-                                      int k, RowC<R>& w) {
-  int id = IC(g, i, j, k);
+struct CPt { R Pb, Tb, beta, uc, grr, gtt, gpp, s1, s2; };
+
+template <typename R>
+__device__ __forceinline__ CPt<R> load_c(const Coef<R>& c, int d, int id) {
+  CPt<R> q;
+  q.Pb = c.Pb[id]; q.Tb = c.Tb[id]; q.beta = c.beta[id];
+  q.uc = d == 0 ? c.uc0[id] : d == 1 ? c.uc1[id] : c.uc2[id];
+  q.grr = c.grr[id]; q.gtt = c.gtt[id]; q.gpp = c.gpp[id];
+  q.s1 = d == 1 ? c.srt[id] : d == 2 ? c.srp[id] : R(0);
+  q.s2 = d == 2 ? c.stp[id] : R(0);
+  return q;
+}
+
+template <typename R>
+__device__ __forceinline__ void row_cw(const Geo<R>& g, const Par& P, const CPt<R>& q, int d, int isT, int i, int j,
+                                       RowC<R>& w) {
   R gm = (R)P.gamma, mu = (R)P.mu;
-  R be = c.beta[id];
-  R alin = isT ? (gm - R(1)) * c.Tb[id] : gm * c.Pb[id];
+  R be = q.beta;
+  R alin = isT ? (gm - R(1)) * q.Tb : gm * q.Pb;
   R visc = isT ? mu * be : mu * (gm - R(1));
   R dif = isT ? be * (R)P.kappa : (gm - R(1)) * (R)P.kappa;
-  R g_rr = c.grr[id], g_tt = c.gtt[id], g_pp = c.gpp[id];
+  R g_rr = q.grr, g_tt = q.gtt, g_pp = q.gpp;
   R tr = g_rr + g_tt + g_pp;
   R ir = g.irc[i];
   w.wp[0] = w.wp[1] = w.wp[2] = R(0);
@@ -158,7 +176,7 @@ __device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<
   w.a = alin + R(2.0 / 3.0) * visc * tr;
   w.dif = dif;
   if (d == 0) {
-    R adv = R(0.5) * c.uc0[id] * g.idr;
+    R adv = R(0.5) * q.uc * g.idr;
     w.adv = adv;
     wa[0] -= adv; wa[2] += adv;
     R f0 = g.rf[i] * g.rf[i], f1 = g.rf[i + 1] * g.rf[i + 1];
@@ -172,7 +190,7 @@ __device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<
     w.wv[1] = -m0 - m1;
   } else if (d == 1) {
     R is = g.isc[j], cot = g.cotc[j];
-    R adv = R(0.5) * c.uc1[id] * ir * g.idth;
+    R adv = R(0.5) * q.uc * ir * g.idth;
     w.adv = adv;
     wa[0] -= adv; wa[2] += adv;
     R f0 = g.sf[j], f1 = g.sf[j + 1];
@@ -180,13 +198,13 @@ __device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<
     w.wT[0] += df * f0; w.wT[1] -= df * (f0 + f1); w.wT[2] += df * f1;
     w.gd[0] = -f0 * ir * is * g.idth;
     w.gd[1] = f1 * ir * is * g.idth;
-    R lin = -visc * (R(2) * g_pp * cot - c.srt[id]) * R(0.5) * ir;
+    R lin = -visc * (R(2) * g_pp * cot - q.s1) * R(0.5) * ir;
     R m0 = R(2) * visc * g_tt * ir * g.idth;
     w.wv[0] = m0 + lin;
     w.wv[1] = -m0 + lin;
   } else {
     R is = g.isc[j], cot = g.cotc[j];
-    R adv = R(0.5) * c.uc2[id] * ir * is * g.idph;
+    R adv = R(0.5) * q.uc * ir * is * g.idph;
     w.adv = adv;
     wa[0] -= adv; wa[2] += adv;
     R df = -dif * ir * ir * is * is * g.idph * g.idph;
@@ -195,24 +213,47 @@ __device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<
     w.gd[1] = ir * is * g.idph;
     // the phi row's coefficient is a - 2 visc G_pp (Appendix B, A2^phi): the
     // -2 visc G_pp part goes with the remaining terms
-    R lin = visc * (c.srp[id] + c.stp[id] * cot) * R(0.5) * ir;
+    R lin = visc * (q.s1 + q.s2 * cot) * R(0.5) * ir;
     R m0 = R(2) * visc * g_pp * ir * is * g.idph;
     w.wv[0] = m0 + lin;
     w.wv[1] = -m0 + lin;
   }
 }
 
-// Normal-velocity row of D_d on the d-face (i,j,k): p at centres m-1, m and
-// u_d on faces m-1, m, m+1.  ubd: the Ubar velocity component d.
 template <typename R>
-__device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<R>& c, const R* ubd, int d, int i,
-                                      int j, int k, R wp[2], R wu[3]) {
-  R mu = (R)P.mu;
+__device__ __forceinline__ void row_c(const Geo<R>& g, const Par& P, const Coef<R>& c, int d, int isT, int i, int j,
+                                      int k, RowC<R>& w) {
+  row_cw(g, P, load_c(c, d, IC(g, i, j, k)), d, isT, i, j, w);
+}
+
+// Normal-velocity row of D_d on the d-face (i,j,k): p at centres m-1, m and
+// u_d on faces m-1, m, m+1.  It reads rho at the two centres and Ubar's u_d on
+// the face.
+template <typename R>
+struct FPt { R rho0, rho1, ub; };
+
+template <typename R>
+__device__ __forceinline__ FPt<R> load_f(const Geo<R>& g, const Coef<R>& c, const R* ubd, int d, int i, int j, int k) {
+  FPt<R> q;
   if (d == 0) {
-    R irh = sdiv(R(2), rho_at(g, c, i - 1, j, k) + rho_at(g, c, i, j, k));
+    q.rho0 = rho_at(g, c, i - 1, j, k); q.rho1 = rho_at(g, c, i, j, k); q.ub = ubd[IRf(g, i, j, k)];
+  } else if (d == 1) {
+    q.rho0 = rho_at(g, c, i, j - 1, k); q.rho1 = rho_at(g, c, i, j, k); q.ub = ubd[ITf(g, i, j, k)];
+  } else {
+    q.rho0 = rho_at(g, c, i, j, k - 1); q.rho1 = rho_at(g, c, i, j, k); q.ub = ubd[IPf(g, i, j, k)];
+  }
+  return q;
+}
+
+template <typename R>
+__device__ __forceinline__ void row_fw(const Geo<R>& g, const Par& P, const FPt<R>& q, int d, int i, int j, R wp[2],
+                                       R wu[3]) {
+  R mu = (R)P.mu;
+  R irh = sdiv(R(2), q.rho0 + q.rho1);
+  if (d == 0) {
     R irf = g.irf[i];
     wp[0] = -irh * g.idr; wp[1] = irh * g.idr;
-    R adv = R(0.5) * ubd[IRf(g, i, j, k)] * g.idr;
+    R adv = R(0.5) * q.ub * g.idr;
     R c0 = g.rc[i - 1] * g.rc[i - 1], c1 = g.rc[i] * g.rc[i];
     R ic0 = g.irc[i - 1] * g.irc[i - 1], ic1 = g.irc[i] * g.irc[i];
     R lap = -mu * irh * irf * irf * g.idr * g.idr;
@@ -222,10 +263,9 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
     wu[1] = -lap * (c0 + c1) - gdv * f0 * (ic1 + ic0);
     wu[2] = adv + lap * c1 + gdv * fp * ic1;
   } else if (d == 1) {
-    R irh = sdiv(R(2), rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
     R ir = g.irc[i], isf = g.isf[j];
     wp[0] = -irh * ir * g.idth; wp[1] = irh * ir * g.idth;
-    R adv = R(0.5) * ubd[ITf(g, i, j, k)] * ir * g.idth;
+    R adv = R(0.5) * q.ub * ir * g.idth;
     R c0 = g.sc[j - 1], c1 = g.sc[j];
     R lap = -mu * irh * ir * ir * isf * g.idth * g.idth;
     R gdv = -mu * irh * R(1.0 / 3.0) * ir * ir * g.idth * g.idth;
@@ -233,34 +273,49 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
     wu[1] = -lap * (c0 + c1) - gdv * g.sf[j] * (g.isc[j] + g.isc[j - 1]);
     wu[2] = adv + lap * c1 + gdv * g.sf[j + 1] * g.isc[j];
   } else {
-    R irh = sdiv(R(2), rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
     R ir = g.irc[i], is = g.isc[j];
     wp[0] = -irh * ir * is * g.idph; wp[1] = irh * ir * is * g.idph;
-    R adv = R(0.5) * ubd[IPf(g, i, j, k)] * ir * is * g.idph;
+    R adv = R(0.5) * q.ub * ir * is * g.idph;
     R lap = -R(4.0 / 3.0) * mu * irh * ir * ir * is * is * g.idph * g.idph;
     wu[0] = -adv + lap; wu[1] = -R(2) * lap; wu[2] = adv + lap;
   }
 }
 
-// Transverse row of D_d for velocity component cc at its location (i,j,k).
 template <typename R>
-__device__ __forceinline__ void row_s(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int cc, int d,
-                                      int i, int j, int k, R w[3]) {
+__device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<R>& c, const R* ubd, int d, int i,
+                                      int j, int k, R wp[2], R wu[3]) {
+  row_fw(g, P, load_f(g, c, ubd, d, i, j, k), d, i, j, wp, wu);
+}
+
+// Transverse row of D_d for velocity component cc at its location (i,j,k): it
+// reads rho at the two centres beside the face and the advecting Ubar component.
+template <typename R>
+struct SPt { R rho0, rho1, ua; };
+
+template <typename R>
+__device__ __forceinline__ SPt<R> load_s(const Geo<R>& g, const Coef<R>& c, const CF<R>& ub, int cc, int d, int i,
+                                         int j, int k) {
+  SPt<R> q;
+  if (cc == 0) { q.rho0 = rho_at(g, c, i - 1, j, k); q.rho1 = rho_at(g, c, i, j, k); }
+  else if (cc == 1) { q.rho0 = rho_at(g, c, i, j - 1, k); q.rho1 = rho_at(g, c, i, j, k); }
+  else { q.rho0 = rho_at(g, c, i, j, k - 1); q.rho1 = rho_at(g, c, i, j, k); }
+  if (cc == 0) q.ua = d == 1 ? R(0.5) * (ht(g, ub.f[2], i - 1, j, k) + ht(g, ub.f[2], i, j, k))
+                             : R(0.5) * (hp(g, ub.f[3], i - 1, j, k) + hp(g, ub.f[3], i, j, k));
+  else if (cc == 1) q.ua = d == 0 ? R(0.5) * (hr(g, ub.f[1], i, j - 1, k) + hr(g, ub.f[1], i, j, k))
+                                  : R(0.5) * (hp(g, ub.f[3], i, j - 1, k) + hp(g, ub.f[3], i, j, k));
+  else q.ua = d == 0 ? R(0.5) * (hr(g, ub.f[1], i, j, k - 1) + hr(g, ub.f[1], i, j, k))
+                     : R(0.5) * (ht(g, ub.f[2], i, j, k - 1) + ht(g, ub.f[2], i, j, k));
+  return q;
+}
+
+template <typename R>
+__device__ __forceinline__ void row_sw(const Geo<R>& g, const Par& P, const SPt<R>& q, int cc, int d, int i, int j,
+                                       R w[3]) {
   R mu = (R)P.mu;
-  R rsum;
-  if (cc == 0) rsum = rho_at(g, c, i - 1, j, k) + rho_at(g, c, i, j, k);
-  else if (cc == 1) rsum = rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k);
-  else rsum = rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k);
-  R irh = sdiv(R(2), rsum);
+  R irh = sdiv(R(2), q.rho0 + q.rho1);
   R ir = cc == 0 ? g.irf[i] : g.irc[i];
   R is = cc == 1 ? g.isf[j] : g.isc[j];
-  R ua;
-  if (cc == 0) ua = d == 1 ? R(0.5) * (ht(g, ub.f[2], i - 1, j, k) + ht(g, ub.f[2], i, j, k))
-                           : R(0.5) * (hp(g, ub.f[3], i - 1, j, k) + hp(g, ub.f[3], i, j, k));
-  else if (cc == 1) ua = d == 0 ? R(0.5) * (hr(g, ub.f[1], i, j - 1, k) + hr(g, ub.f[1], i, j, k))
-                                : R(0.5) * (hp(g, ub.f[3], i, j - 1, k) + hp(g, ub.f[3], i, j, k));
-  else ua = d == 0 ? R(0.5) * (hr(g, ub.f[1], i, j, k - 1) + hr(g, ub.f[1], i, j, k))
-                   : R(0.5) * (ht(g, ub.f[2], i, j, k - 1) + ht(g, ub.f[2], i, j, k));
+  R ua = q.ua;
   if (d == 0) {
     R adv = R(0.5) * ua * g.idr, lap = -mu * irh * ir * ir * g.idr * g.idr;
     R f0 = g.rf[i] * g.rf[i], f1 = g.rf[i + 1] * g.rf[i + 1];
@@ -273,6 +328,12 @@ __device__ __forceinline__ void row_s(const Geo<R>& g, const Par& P, const Coef<
     R adv = R(0.5) * ua * ir * is * g.idph, lap = -mu * irh * ir * ir * is * is * g.idph * g.idph;
     w[0] = -adv + lap; w[1] = -R(2) * lap; w[2] = adv + lap;
   }
+}
+
+template <typename R>
+__device__ __forceinline__ void row_s(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int cc, int d,
+                                      int i, int j, int k, R w[3]) {
+  row_sw(g, P, load_s(g, c, ub, cc, d, i, j, k), cc, d, i, j, w);
 }
 
 }  // namespace sph

@@ -2,6 +2,11 @@
 update, divergence and cyclic corrections) against the FP64 oracle and the
 FP64 library path.
 
+The sweeps of the mixed mode take the partitioned line solver (one warp per
+line, chunk elimination + parallel cyclic reduction across the lanes) for
+lines of 64, 128 or 256 cells and the thread-per-line block Thomas solver
+otherwise; both are checked here.
+
 Bounds:
 * each FP32 line solve: 1e-5 relative (max norm per field) against the oracle;
 * the right-hand side: 1e-5 relative per field against the oracle, plus the
@@ -19,7 +24,7 @@ import oracle
 import paper_2004_13887_gb300 as sph
 from inputs import cases
 from tests.gpu_helpers import perturbed, rel_err, solver_for, to_dev, to_host
-from tests.test_gpu_parity import CASES, rhs_midpoint
+from tests.test_gpu_parity import CASES, _bubble, _sector, _shell, rhs_midpoint
 
 pytestmark = pytest.mark.gpu
 MIXED = sph.SPH_PREC_MIXED
@@ -118,3 +123,79 @@ def test_mixed_steps_full_size_bubble():
     print("mixed vs fp64, 20 steps:", errs)
     for k, v in errs.items():
         assert v <= 1e-6, (k, v)
+
+
+# Line lengths 64, 128, 256 in every direction (chunks of 2, 4, 8 cells per
+# lane), periodic and walled phi, a pole, and a direction of another length
+# (40: block Thomas) next to partitioned ones.
+PART_CASES = {
+    "bubble_64x64x128": lambda: _bubble((64, 64, 128)),
+    "shell_64x128x256": lambda: _shell((64, 128, 256), pole=False),
+    "shell_pole_128x64x64": lambda: _shell((128, 64, 64), pole=True),
+    "sector_40x256x64": lambda: _sector((40, 256, 64)),
+}
+
+
+@pytest.mark.parametrize("name", list(PART_CASES))
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_partitioned_sweep_vs_oracle(name, d):
+    g, par, bg, Un, Uk, S, dt = PART_CASES[name]()
+    s = solver_for(g, par, bg, Un, precision=MIXED)
+    s.set_iterate(Uk)
+    rhs = perturbed(g.zeros(), [1.0] * 5, 30 + d, g)
+    x = to_host(s.sweep(d, dt, to_dev(rhs)))
+    ref = oracle.sweep(g, par, Un, Uk, dt, d, rhs, bg=bg)
+    for q in range(5):
+        assert rel_err(x[q], ref[q]) <= 1e-5, (name, d, q, rel_err(x[q], ref[q]))
+
+
+def test_line_solver_option():
+    g, par, bg, Un, Uk, S, dt = PART_CASES["shell_64x128x256"]()
+    s = solver_for(g, par, bg, Un, precision=MIXED)
+    with pytest.raises(sph.SphError):
+        s.set_line_solver(7)
+    s.set_iterate(Uk)
+    rhs = to_dev(perturbed(g.zeros(), [1.0] * 5, 40, g))
+    for d in range(3):
+        xp = to_host(s.sweep(d, dt, rhs))
+        s.set_line_solver(sph.SPH_LINES_THOMAS)
+        xt = to_host(s.sweep(d, dt, rhs))
+        s.set_line_solver(sph.SPH_LINES_PARTITIONED)
+        for q in range(5):
+            assert rel_err(xp[q], xt[q]) <= 1e-5, (d, q, rel_err(xp[q], xt[q]))
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_partitioned_sweep_full_size(d):
+    """The benchmark grid (128 x 256 x 256: chunks of 4, 8, 8): the mixed sweep
+    against the FP64 library sweep on the same inputs, every point."""
+    c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
+    it = perturbed(c.init, [5.0, 1e-2, 1e-2, 1e-2, 1e-2], 9, c.grid)
+    rhs = to_dev(perturbed(c.grid.zeros(), [1.0] * 5, 50 + d, c.grid))
+    xs = []
+    for prec in (sph.SPH_PREC_FP64, MIXED):
+        s = solver_for(c.grid, c.par, c.bg, c.init, precision=prec)
+        s.set_iterate(it)
+        xs.append(to_host(s.sweep(d, c.dt, rhs)))
+        s.close()
+    for q in range(5):
+        assert rel_err(xs[1][q], xs[0][q]) <= 1e-5, (d, q, rel_err(xs[1][q], xs[0][q]))
+
+
+def test_partitioned_steps_cyclic():
+    """Whole steps on a periodic shell: partitioned vs Thomas vs FP64."""
+    g, par, bg, Un, Uk, S, dt = PART_CASES["shell_64x128x256"]()
+    outs = []
+    for prec, which in ((sph.SPH_PREC_FP64, None), (MIXED, sph.SPH_LINES_THOMAS), (MIXED, sph.SPH_LINES_PARTITIONED)):
+        s = solver_for(g, par, bg, Un, precision=prec)
+        if which is not None:
+            s.set_line_solver(which)
+        for _ in range(5):
+            s.step(dt, 2, S)
+        outs.append(to_host(s.get_state()))
+        s.close()
+    for q in range(5):
+        scale = float(np.max(np.abs(outs[0][q] - Un[q]))) or 1.0
+        for o in outs[1:]:
+            err = float(np.max(np.abs(o[q] - outs[0][q])))
+            assert err <= 1e-5 * scale, (q, err, scale)
