@@ -40,10 +40,25 @@ using namespace sph;
 
 // ------------------------------------------------------------------ kernels
 
+// Ubar = (U^n + U^k)/2 for the five fields in one launch (blockIdx.y = field),
+// two values per thread per pass (16-byte loads, 8-byte stores in FP32).
 template <typename R>
-__global__ void k_avg(long n, const double* __restrict__ a, const double* __restrict__ b, R* __restrict__ o) {
+struct AvgArgs { const double* a[5]; const double* b[5]; R* o[5]; long n[5]; };
+
+template <typename R>
+__global__ void k_avg(AvgArgs<R> A) {
+  const int f = blockIdx.y;
+  const double* __restrict__ a = A.a[f];
+  const double* __restrict__ b = A.b[f];
+  R* __restrict__ o = A.o[f];
+  long n = A.n[f], n2 = n >> 1;
   long s = (long)gridDim.x * blockDim.x;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = (R)(0.5 * (a[t] + b[t]));
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += s) {
+    double2 x = reinterpret_cast<const double2*>(a)[t], y = reinterpret_cast<const double2*>(b)[t];
+    o[2 * t] = (R)(0.5 * (x.x + y.x));
+    o[2 * t + 1] = (R)(0.5 * (x.y + y.y));
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) o[n - 1] = (R)(0.5 * (a[n - 1] + b[n - 1]));
 }
 
 template <typename R>
@@ -65,15 +80,20 @@ __global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
   if (t >= N) return;
   int k = t % g.np, j = (t / g.np) % g.nt, i = t / (g.np * g.nt);
   const R *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
-  // thermodynamics in FP64 from background + perturbation
-  double pref = g.bgp[i + 1] + P.pinf, Tref = g.bgT[i + 1];
-  double pp = (double)ub.f[0][t], Tp = (double)ub.f[4][t];
-  double pb = pref + pp, tb = Tref + Tp;
-  c.Pb[t] = (R)pb;
-  c.Tb[t] = (R)tb;
-  c.rho[t] = (R)(pb / (P.Rg * tb));
-  c.drho[t] = (R)((pp * Tref - pref * Tp) / (P.Rg * Tref * tb));
-  c.beta[t] = (R)((P.gamma - 1.0) * tb / pb);
+  // thermodynamics from background + perturbation.  The density perturbation
+  // rho - rho_ref = (p' T_ref - (p_ref + pi_inf) T') / (Rg T_ref T) has no
+  // cancellation between large terms, so the bulk type keeps its relative
+  // precision for it.
+  R pref = (R)(g.bgp[i + 1] + P.pinf), Tref = (R)g.bgT[i + 1];
+  R pp = ub.f[0][t], Tp = ub.f[4][t];
+  R pb = pref + pp, tb = Tref + Tp;
+  R iRg = (R)(1.0 / P.Rg);
+  R itb = sdiv(R(1), tb);
+  c.Pb[t] = pb;
+  c.Tb[t] = tb;
+  c.rho[t] = pb * itb * iRg;
+  c.drho[t] = sdiv((pp * Tref - pref * Tp) * itb * iRg, Tref);
+  c.beta[t] = sdiv((R)(P.gamma - 1.0) * tb, pb);
   R ur = hr(g, UR, i, j, k), ut = ht(g, UT, i, j, k), up = hp(g, UP, i, j, k);
   c.uc0[t] = ur; c.uc1[t] = ut; c.uc2[t] = up;
   R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j], h = R(0.5);
@@ -1083,12 +1103,15 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
   if (sizeof(R) == sizeof(double) && !have_iter) {
     for (int f = 0; f < 5; f++) ub.f[f] = (const R*)un[f];
   } else {
+    AvgArgs<R> A;
+    long mx = 0;
     for (int f = 0; f < 5; f++) {
-      long n = (long)c->nf[f];
-      k_begin(c, SPH_K_AVG);
-      k_avg<R><<<grid_stride_blocks(n), 256, 0, c->st>>>(n, un[f], uk[f], b.Ub[f]);
-      if (launch_ok(c)) return SPH_ERR_CUDA;
+      A.a[f] = un[f]; A.b[f] = uk[f]; A.o[f] = b.Ub[f]; A.n[f] = (long)c->nf[f];
+      if (A.n[f] > mx) mx = A.n[f];
     }
+    k_begin(c, SPH_K_AVG);
+    k_avg<R><<<dim3(grid_stride_blocks((mx + 1) / 2) / 4 + 1, 5), 256, 0, c->st>>>(A);
+    if (launch_ok(c)) return SPH_ERR_CUDA;
     ub = cf_of(b.Ub);
   }
   k_begin(c, SPH_K_COEF);
@@ -1175,7 +1198,7 @@ static int lines_ok(const sph_ctx* c, int d) {
 template <int D, int P>
 static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
   constexpr int NW = 32 / P, NT = 32 * NW;
-  const size_t smb = (size_t)lines::blk_fields(P) * lines::FS * sizeof(float);
+  const size_t smb = (size_t)lines::NFB * lines::FS * sizeof(float);
   const size_t sms = (size_t)lines::NFS * lines::FS * sizeof(float);
   int ng, e;
   k_begin(c, SPH_K_SWEEP_R + D);
