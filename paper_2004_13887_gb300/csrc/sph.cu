@@ -42,8 +42,30 @@ using namespace sph;
 
 // Ubar = (U^n + U^k)/2 for the five fields in one launch (blockIdx.y = field),
 // two values per thread per pass (16-byte loads, 8-byte stores in FP32).
+// Ubar = (a + b)/2 and D = b - a (a = U^n, b = U^{n+1,k}; D is the -(U^k - U^n)
+// part of the right-hand side, so that stage reads neither FP64 state).  In
+// FP32 mode both are formed as pairs on the FP32 pipe: o = Ubar rounded, and
+// for the velocity components lo[f] (when not null) = the remainder, so that
+// div(Ubar) can be formed to ~48 bits; D is rounded once from the exact pair.
 template <typename R>
-struct AvgArgs { const double* a[5]; const double* b[5]; R* o[5]; long n[5]; };
+struct AvgArgs { const double* a[5]; const double* b[5]; R* o[5]; R* lo[5]; R* d[5]; long n[5]; };
+
+template <typename R>
+__device__ __forceinline__ void avg1(const double x, const double y, R* o, R* lo, R* d, long t) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    o[t] = (R)(0.5 * (x + y));
+    d[t] = (R)(y - x);
+  } else {
+    float xh, xl, yh, yl, h, l;
+    d2ff(x, xh, xl);
+    d2ff(y, yh, yl);
+    ff_add(xh, xl, yh, yl, h, l);
+    o[t] = 0.5f * h;
+    if (lo) lo[t] = 0.5f * l;
+    ff_sub(yh, yl, xh, xl, h, l);
+    d[t] = h + l;
+  }
+}
 
 template <typename R>
 __global__ void k_avg(AvgArgs<R> A) {
@@ -51,14 +73,16 @@ __global__ void k_avg(AvgArgs<R> A) {
   const double* __restrict__ a = A.a[f];
   const double* __restrict__ b = A.b[f];
   R* __restrict__ o = A.o[f];
+  R* __restrict__ lo = A.lo[f];
+  R* __restrict__ d = A.d[f];
   long n = A.n[f], n2 = n >> 1;
   long s = (long)gridDim.x * blockDim.x;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += s) {
     double2 x = reinterpret_cast<const double2*>(a)[t], y = reinterpret_cast<const double2*>(b)[t];
-    o[2 * t] = (R)(0.5 * (x.x + y.x));
-    o[2 * t + 1] = (R)(0.5 * (x.y + y.y));
+    avg1(x.x, y.x, o, lo, d, 2 * t);
+    avg1(x.y, y.y, o, lo, d, 2 * t + 1);
   }
-  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) o[n - 1] = (R)(0.5 * (a[n - 1] + b[n - 1]));
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) avg1(a[n - 1], b[n - 1], o, lo, d, n - 1);
 }
 
 template <typename R>
@@ -84,16 +108,16 @@ __global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
   // rho - rho_ref = (p' T_ref - (p_ref + pi_inf) T') / (Rg T_ref T) has no
   // cancellation between large terms, so the bulk type keeps its relative
   // precision for it.
-  R pref = (R)(g.bgp[i + 1] + P.pinf), Tref = (R)g.bgT[i + 1];
+  R pref = g.pcen[i], Tref = g.Tcen[i];
   R pp = ub.f[0][t], Tp = ub.f[4][t];
   R pb = pref + pp, tb = Tref + Tp;
-  R iRg = (R)(1.0 / P.Rg);
+  R iRg = pick<R>(1.0 / P.Rg, P.iRg_f);
   R itb = sdiv(R(1), tb);
   c.Pb[t] = pb;
   c.Tb[t] = tb;
   c.rho[t] = pb * itb * iRg;
   c.drho[t] = sdiv((pp * Tref - pref * Tp) * itb * iRg, Tref);
-  c.beta[t] = sdiv((R)(P.gamma - 1.0) * tb, pb);
+  c.beta[t] = sdiv((pick<R>(P.gamma, P.gamma_f) - R(1)) * tb, pb);
   R ur = hr(g, UR, i, j, k), ut = ht(g, UT, i, j, k), up = hp(g, UP, i, j, k);
   c.uc0[t] = ur; c.uc1[t] = ut; c.uc2[t] = up;
   R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j], h = R(0.5);
@@ -127,16 +151,48 @@ __device__ __forceinline__ double div_ubar(const Geo<double>& g, const CF<double
   return 0.5 * (dr_ + dt_ + dp_);
 }
 
+// div(Ubar) at centre (i,j,k) in FP32 mode, from the pair (hi = Ubar, lo) of the
+// velocity components: each face flux and each difference is carried as a pair,
+// so the cancellation of nearly equal fluxes (and of the three directions
+// against each other) at low Mach number costs no accuracy.
+__device__ __forceinline__ float div_ubar_ff(const Geo<float>& g, const CF<float>& ub, const CF<float>& ul, int i,
+                                             int j, int k) {
+  int a0 = IRf(g, i, j, k), a1 = IRf(g, i + 1, j, k);
+  int b0 = ITf(g, i, j, k), b1 = ITf(g, i, j + 1, k);
+  int kp = g.per ? wrapk(g, k + 1) : k + 1;
+  int c0 = IPf(g, i, j, k), c1 = IPf(g, i, j, kp);
+  float ir = g.irc[i], is = g.isc[j];
+  float h0, l0, h1, l1, dh, dl, th, tl, sh, sl;
+  // r: (rf1^2 u1 - rf0^2 u0) / rc^2 / dr
+  ff_mul(g.rf2h[i + 1], g.rf2l[i + 1], ub.f[1][a1], ul.f[1][a1], h1, l1);
+  ff_mul(g.rf2h[i], g.rf2l[i], ub.f[1][a0], ul.f[1][a0], h0, l0);
+  ff_sub(h1, l1, h0, l0, dh, dl);
+  float cr = ir * ir * g.idr;
+  ff_mul(dh, dl, cr, 0.f, sh, sl);
+  // theta: (sf1 u1 - sf0 u0) / (rc sc dtheta)
+  ff_mul(g.sfh[j + 1], g.sfl[j + 1], ub.f[2][b1], ul.f[2][b1], h1, l1);
+  ff_mul(g.sfh[j], g.sfl[j], ub.f[2][b0], ul.f[2][b0], h0, l0);
+  ff_sub(h1, l1, h0, l0, dh, dl);
+  ff_mul(dh, dl, ir * is * g.idth, 0.f, th, tl);
+  ff_add(sh, sl, th, tl, sh, sl);
+  // phi: (u1 - u0) / (rc sc dphi)
+  ff_sub(ub.f[3][c1], ul.f[3][c1], ub.f[3][c0], ul.f[3][c0], dh, dl);
+  ff_mul(dh, dl, ir * is * g.idph, 0.f, th, tl);
+  ff_add(sh, sl, th, tl, sh, sl);
+  return sh + sl;
+}
+
 // R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per centre.
 template <typename R>
-__global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<double> un,
-                                               CF<double> uk, CF<double> src, int has_src, double tau, MF<R> Rout) {
+__global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
+                                               CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
+                                               int has_src, R tau, MF<R> Rout) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int N = g.nr * g.nt * g.np;
   if (t >= N) return;
   int k = t % g.np, j = (t / g.np) % g.nt, i = t / (g.np * g.nt);
   const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
-  R mu = (R)P.mu, gm = (R)P.gamma, h = R(0.5);
+  R mu = pick<R>(P.mu, P.mu_f), gm = pick<R>(P.gamma, P.gamma_f), h = R(0.5);
   R ir = g.irc[i], is = g.isc[j];
   R accp = R(0), accT = R(0);
   R ap = R(0), aT = R(0);
@@ -163,7 +219,9 @@ __global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, 
     if (d == 0) accT += w.adv * g.dbgT[i] - w.dif * g.lapT[i];
     aT = w.a;
   }
-  double divu = div_ubar(gd, un, uk, i, j, k);
+  R divu;
+  if constexpr (sizeof(R) == sizeof(double)) divu = div_ubar(gd, un, uk, i, j, k);
+  else divu = div_ubar_ff(g, ub, ul, i, j, k);
   R xrt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr
         + (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth;
   R xrp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr
@@ -173,17 +231,18 @@ __global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, 
   R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
   accp += -mu * (gm - R(1)) * cross;
   accT += -mu * c.beta[t] * cross;
-  double Np = (double)ap * divu + (double)accp, NT = (double)aT * divu + (double)accT;
-  double sp = has_src ? src.f[0][t] : 0.0, sT = has_src ? src.f[4][t] : 0.0;
-  Rout.f[0][t] = (R)(-(uk.f[0][t] - un.f[0][t]) - tau * (Np - sp));
-  Rout.f[4][t] = (R)(-(uk.f[4][t] - un.f[4][t]) - tau * (NT - sT));
+  R Np = ap * divu + accp, NT = aT * divu + accT;
+  if (has_src) { Np -= to_bulk<R>(src.f[0][t]); NT -= to_bulk<R>(src.f[4][t]); }
+  R d0 = hasD ? D.f[0][t] : R(0), d4 = hasD ? D.f[4][t] : R(0);
+  Rout.f[0][t] = -d0 - tau * Np;
+  Rout.f[4][t] = -d4 - tau * NT;
 }
 
 // R for the momentum row of component D on its faces: one thread per face
 // (zero on wall faces, which are not unknowns).
 template <typename R, int D>
-__global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<double> un, CF<double> uk,
-                                               CF<double> src, int has_src, double tau, MF<R> Rout) {
+__global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<R> Dv, int hasD,
+                                               CF<double> src, int has_src, R tau, MF<R> Rout) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   int ni = g.nr + (D == 0), nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
   if (t >= ni * nj * nk) return;
@@ -191,7 +250,7 @@ __global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R>
   bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
   if (wall) { Rout.f[1 + D][t] = R(0); return; }
   const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
-  R mu = (R)P.mu, om = (R)P.omega, h = R(0.5);
+  R mu = pick<R>(P.mu, P.mu_f), om = pick<R>(P.omega, P.omega_f), h = R(0.5);
   R wp[2], wu[3], w[3];
   R acc;
   if (D == 0) {
@@ -206,7 +265,7 @@ __global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R>
     int c0 = IC(g, i - 1, j, k), c1 = IC(g, i, j, k);
     R rs = c.rho[c0] + c.rho[c1];
     R bf = sdiv(c.drho[c0] + c.drho[c1], rs);
-    acc += (R(1) - bf) * g.ehyd[i] + (R)P.g * bf;
+    acc += (R(1) - bf) * g.ehyd[i] + pick<R>(P.g, P.g_f) * bf;
     // D_M
     R irf = g.irf[i], s = g.sc[j], is = g.isc[j];
     R irh = sdiv(R(2), rs);
@@ -276,8 +335,9 @@ __global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R>
          - mu * irh * (R(2) * ir * ir * is * g.idph * (hr(g, UR, i, j, k) - hr(g, UR, i, j, k - 1))
                        + R(2) * cj * ir * ir * is * is * g.idph * (ht(g, UT, i, j, k) - ht(g, UT, i, j, k - 1)));
   }
-  double sv = has_src ? src.f[1 + D][t] : 0.0;
-  Rout.f[1 + D][t] = (R)(-(uk.f[1 + D][t] - un.f[1 + D][t]) - tau * ((double)acc - sv));
+  if (has_src) acc -= to_bulk<R>(src.f[1 + D][t]);
+  R dd = hasD ? Dv.f[1 + D][t] : R(0);
+  Rout.f[1 + D][t] = -dd - tau * acc;
 }
 
 // ------------------------------------------------------------ line solvers
@@ -388,16 +448,19 @@ struct SweepArgs {
   int* flag;
 };
 
-// store a value of field f at flat index idx: x (mode 0) or uk = base + v (mode 1)
-template <typename R>
-__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, int idx, double v, double* ss, int* bad) {
+// store a value of field f at flat index idx: x (mode 0) or uk = base + v (mode
+// 1, the one FP64 add per value of the mixed path), with the square of v summed
+// in the bulk type
+template <typename R, typename V>
+__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, int idx, V v, R* ss, int* bad) {
   if (!A.update) {
     A.x.f[f][idx] = (R)v;
   } else {
-    double nv = A.base.f[f][idx] + v;
+    double nv = A.base.f[f][idx] + f2d(v);
     if (!isfinite(nv)) *bad |= FLAG_NONFINITE;
     A.uk.f[f][idx] = nv;
-    ss[f] += v * v;
+    R r = (R)v;
+    ss[f] += r * r;
   }
 }
 // wall face of field f: x = 0, or uk = base (mode 1)
@@ -408,7 +471,7 @@ __device__ __forceinline__ void put_wall(const SweepArgs<R>& A, int f, int idx) 
 }
 
 template <typename R, int D>
-__device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, double* ss, int* bad) {
+__device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, R* ss, int* bad) {
   const Geo<R>& g = S.g;
   constexpr int d = D;
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
@@ -504,12 +567,12 @@ __device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, double
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
       int ic = IC(g, i, j, k);
-      put(S, 0, ic, (double)xs[0], ss, bad);
-      put(S, 4, ic, (double)xs[1], ss, bad);
+      put(S, 0, ic, xs[0], ss, bad);
+      put(S, 4, ic, xs[1], ss, bad);
       if (m < n - 1) {
         int fi = i, fj = j, fk = k;
         if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = m + 1;
-        put(S, 1 + d, face_idx(g, d, fi, fj, fk), (double)xs[2], ss, bad);
+        put(S, 1 + d, face_idx(g, d, fi, fj, fk), xs[2], ss, bad);
       } else {
         int fi = i, fj = j, fk = k;
         if (d == 0) fi = n; else if (d == 1) fj = n; else fk = n;
@@ -563,9 +626,8 @@ __host__ __device__ constexpr int trans_comp(int d, int kind) {
 
 // output of a transverse line value at cell m, plus the wall faces of that
 // component next to the first / last line
-template <typename R>
-__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, double v, double* ss,
-                                           int* bad) {
+template <typename R, typename V>
+__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, V v, R* ss, int* bad) {
   const Geo<R>& g = S.g;
   put(S, 1 + cc, face_idx(g, cc, i, j, k), v, ss, bad);
   int lo = (cc == 0) ? (i == 1) : (cc == 1) ? (j == 1) : (k == 1);
@@ -584,7 +646,7 @@ __device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i,
 }
 
 template <typename R, int D, int KIND>
-__device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, double* ss, int* bad) {
+__device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, R* ss, int* bad) {
   const Geo<R>& g = S.g;
   constexpr int d = D, kind = KIND;
   int cc = trans_comp(d, kind);
@@ -630,7 +692,7 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, doubl
       }
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);
-      scalar_put(S, cc, i, j, k, (double)xy, ss, bad);
+      scalar_put(S, cc, i, j, k, xy, ss, bad);
     }
     return;
   }
@@ -663,7 +725,7 @@ template <typename R, int D>
 __global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
   int kind = blockIdx.y;
   int line = blockIdx.x * blockDim.x + threadIdx.x;
-  double ss[5] = {0, 0, 0, 0, 0};
+  R ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   if (line < S.nl[kind]) {
     int a = (int)(line / S.nb[kind]) + S.a0[kind];
@@ -675,9 +737,9 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
   if (bad) atomicOr(S.flag, bad);
   if (S.update) {
     for (int f = 0; f < 5; f++) {
-      double v = ss[f];
+      R v = ss[f];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(S.acc + f, v);
+      if ((threadIdx.x & 31) == 0 && v != R(0)) atomicAdd(S.acc + f, f2d(v));
     }
   }
 }
@@ -690,8 +752,11 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
 template <typename R>
 struct Bufs {
   R* metric;       // rc rf irc irf | sc sf isc isf cc cf cotc cotf (bulk type)
-  R* bgder;        // dbgp dbgT lapT rhoref (nr each) ehyd (nr+1)
+  R* bgder;        // dbgp dbgT lapT rhoref (nr each) ehyd (nr+1) pcen Tcen (nr each)
+  R* mdf;          // rf^2 hi, lo (nr+1 each), sin(theta_f) hi, lo (nt+1 each)
   R* Ub[5];
+  R* UbLo[5];      // FP32 mode: remainders of the velocity components of Ubar (1-3)
+  R* Db[5];        // U^{n+1,k} - U^n
   R* Rb[5];
   R* X1[5];
   R* coef;
@@ -776,8 +841,10 @@ static void prof_free(sph_ctx* c) {
 
 template <typename R>
 static void bufs_free(Bufs<R>& b) {
-  cudaFree(b.metric); cudaFree(b.bgder); cudaFree(b.coef); cudaFree(b.scr);
-  for (int f = 0; f < 5; f++) { cudaFree(b.Ub[f]); cudaFree(b.Rb[f]); cudaFree(b.X1[f]); }
+  cudaFree(b.metric); cudaFree(b.bgder); cudaFree(b.mdf); cudaFree(b.coef); cudaFree(b.scr);
+  for (int f = 0; f < 5; f++) {
+    cudaFree(b.Ub[f]); cudaFree(b.UbLo[f]); cudaFree(b.Db[f]); cudaFree(b.Rb[f]); cudaFree(b.X1[f]);
+  }
 }
 
 static void free_all(sph_ctx* c) {
@@ -834,15 +901,20 @@ static void set_geo_ptrs(Bufs<R>& b, const Geo<double>& base, const double* bg, 
   g.bgp = bg; g.bgT = bg + (nr + 2);
   g.dbgp = b.bgder; g.dbgT = b.bgder + nr; g.lapT = b.bgder + 2 * nr; g.rhoref = b.bgder + 3 * nr;
   g.ehyd = b.bgder + 4 * nr;
+  g.pcen = b.bgder + 5 * nr + 1; g.Tcen = b.bgder + 6 * nr + 1;
+  g.rf2h = b.mdf; g.rf2l = b.mdf + (nr + 1); g.sfh = b.mdf + 2 * (nr + 1); g.sfl = b.mdf + 2 * (nr + 1) + (nt + 1);
 }
 
 template <typename R>
 static int bufs_alloc(Bufs<R>& b, size_t nmet, int nr, const size_t* nf, long N, size_t nscr, int bulk) {
 #define ALLOC(p, n) do { if (!cuda_ok(cudaMalloc((void**)&(p), (size_t)(n) * sizeof(R)))) return SPH_ERR_NOMEM; } while (0)
   ALLOC(b.metric, nmet);
-  ALLOC(b.bgder, 5 * (size_t)nr + 1);
+  ALLOC(b.bgder, 7 * (size_t)nr + 1);
+  ALLOC(b.mdf, nmet);
   if (!bulk) return SPH_OK;
-  for (int f = 0; f < 5; f++) { ALLOC(b.Ub[f], nf[f]); ALLOC(b.Rb[f], nf[f]); ALLOC(b.X1[f], nf[f]); }
+  for (int f = 0; f < 5; f++) { ALLOC(b.Ub[f], nf[f]); ALLOC(b.Db[f], nf[f]); ALLOC(b.Rb[f], nf[f]); ALLOC(b.X1[f], nf[f]); }
+  if (sizeof(R) == sizeof(float))
+    for (int f = 1; f < 4; f++) ALLOC(b.UbLo[f], nf[f]);
   ALLOC(b.coef, (size_t)NCOEF * N);
   ALLOC(b.scr, nscr);
 #undef ALLOC
@@ -856,7 +928,7 @@ static int bufs_alloc(Bufs<R>& b, size_t nmet, int nr, const size_t* nf, long N,
 
 template <typename R>
 static int upload_tables(sph_ctx* c, Bufs<R>& b, const double* hmet, const double* hder, int nr) {
-  size_t nd = 5 * (size_t)nr + 1;
+  size_t nd = 7 * (size_t)nr + 1;
   R* tm = (R*)malloc(c->nmet * sizeof(R));
   R* td = (R*)malloc(nd * sizeof(R));
   if (!tm || !td) { free(tm); free(td); return SPH_ERR_NOMEM; }
@@ -866,6 +938,15 @@ static int upload_tables(sph_ctx* c, Bufs<R>& b, const double* hmet, const doubl
   if (!cuda_ok(cudaMemcpy(b.metric, tm, c->nmet * sizeof(R), cudaMemcpyHostToDevice)) ||
       !cuda_ok(cudaMemcpy(b.bgder, td, nd * sizeof(R), cudaMemcpyHostToDevice)))
     e = SPH_ERR_CUDA;
+  // rf^2 and sin(theta_f) as hi + lo pairs (tm has room: nmet > 2 (nr+1) + 2 (nt+1))
+  int nt = c->d64.g.nt;
+  const double* rf = hmet + (nr + 1);
+  const double* sf = hmet + 4 * (nr + 1) + (nt + 1);
+  R* rh = tm; R* rl = tm + (nr + 1); R* sh = tm + 2 * (nr + 1); R* sl = sh + (nt + 1);
+  for (int i = 0; i <= nr; i++) { double v = rf[i] * rf[i]; rh[i] = (R)v; rl[i] = (R)(v - (double)rh[i]); }
+  for (int j = 0; j <= nt; j++) { double v = sf[j]; sh[j] = (R)v; sl[j] = (R)(v - (double)sh[j]); }
+  size_t nm = 2 * (size_t)(nr + 1) + 2 * (size_t)(nt + 1);
+  if (e == SPH_OK && !cuda_ok(cudaMemcpy(b.mdf, tm, nm * sizeof(R), cudaMemcpyHostToDevice))) e = SPH_ERR_CUDA;
   free(tm); free(td);
   return e;
 }
@@ -876,10 +957,11 @@ static int upload_background(sph_ctx* c, const double* pref, const double* Tref)
   int nr = g.nr;
   const double* rc = c->hmet;
   const double* rf = rc + (nr + 1);
-  double* der = (double*)calloc(5 * (size_t)nr + 1, sizeof(double));
+  double* der = (double*)calloc(7 * (size_t)nr + 1, sizeof(double));
   if (!der) return SPH_ERR_NOMEM;
   double* dbgp = der; double* dbgT = der + nr; double* lapT = der + 2 * nr; double* rhoref = der + 3 * nr;
   double* ehyd = der + 4 * nr;
+  double* pcen = der + 5 * nr + 1; double* Tcen = der + 6 * nr + 1;
   double Rg = c->P.Rg, pinf = c->P.pinf;
   for (int i = 0; i < nr; i++) {
     // index i+1 of the tables is centre i; 0 and nr+1 are the ghosts
@@ -888,6 +970,8 @@ static int upload_background(sph_ctx* c, const double* pref, const double* Tref)
     double f0 = rf[i] * rf[i], f1 = rf[i + 1] * rf[i + 1];
     lapT[i] = (f1 * (Tref[i + 2] - Tref[i + 1]) - f0 * (Tref[i + 1] - Tref[i])) / (rc[i] * rc[i] * g.dr * g.dr);
     rhoref[i] = Tref[i + 1] != 0.0 ? (pref[i + 1] + pinf) / (Rg * Tref[i + 1]) : 0.0;
+    pcen[i] = pref[i + 1] + pinf;
+    Tcen[i] = Tref[i + 1];
   }
   for (int i = 1; i < nr; i++) {
     double rf_ = 0.5 * (rhoref[i - 1] + rhoref[i]);
@@ -926,6 +1010,8 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   P.omega = pa->omega;
   P.kappa = pa->mu * pa->gamma * pa->cv / pa->Pr;
   P.Rg = pa->cv * (pa->gamma - 1.0);
+  P.gamma_f = (float)P.gamma; P.mu_f = (float)P.mu; P.kappa_f = (float)P.kappa; P.g_f = (float)P.g;
+  P.omega_f = (float)P.omega; P.iRg_f = (float)(1.0 / P.Rg);
   c->N = (long)g.nr * g.nt * g.np;
   for (int f = 0; f < 5; f++) c->nf[f] = sph_field_size(gr, f);
   c->unknowns[0] = c->unknowns[4] = c->N;
@@ -1106,7 +1192,8 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
     AvgArgs<R> A;
     long mx = 0;
     for (int f = 0; f < 5; f++) {
-      A.a[f] = un[f]; A.b[f] = uk[f]; A.o[f] = b.Ub[f]; A.n[f] = (long)c->nf[f];
+      A.a[f] = un[f]; A.b[f] = uk[f]; A.o[f] = b.Ub[f]; A.lo[f] = b.UbLo[f]; A.d[f] = b.Db[f];
+      A.n[f] = (long)c->nf[f];
       if (A.n[f] > mx) mx = A.n[f];
     }
     k_begin(c, SPH_K_AVG);
@@ -1121,21 +1208,22 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
   return SPH_OK;
 }
 
+// The right-hand side stage: centre rows, then the momentum rows of each
+// component (timed as one stage).
 template <typename R>
-static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, double tau, CF<double> src, int has_src, MF<R> Rout) {
+static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, double tau, CF<double> src, int has_src,
+                   MF<R> Rout) {
   CF<double> un = cf_of(c->U[c->cur]);
+  CF<R> Dv = cf_of(b.Db);  // U^k - U^n from the averaging stage (zero, and not read, when hasD = 0)
+  CF<R> ul = sizeof(R) == sizeof(float) ? cf_of(b.UbLo) : ub;  // velocity remainders of Ubar (FP32 mode)
+  R tr = (R)tau;
   k_begin(c, SPH_K_RHS);
-  k_rhs_c<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, un, uk, src, has_src,
-                                                                  tau, Rout);
-  if (launch_ok(c)) return SPH_ERR_CUDA;
-  k_begin(c, SPH_K_RHS);
-  k_rhs_u<R, 0><<<(unsigned)((c->nf[1] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, un, uk, src, has_src, tau, Rout);
-  if (launch_ok(c)) return SPH_ERR_CUDA;
-  k_begin(c, SPH_K_RHS);
-  k_rhs_u<R, 1><<<(unsigned)((c->nf[2] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, un, uk, src, has_src, tau, Rout);
-  if (launch_ok(c)) return SPH_ERR_CUDA;
-  k_begin(c, SPH_K_RHS);
-  k_rhs_u<R, 2><<<(unsigned)((c->nf[3] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, un, uk, src, has_src, tau, Rout);
+  k_rhs_c<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD,
+                                                                  src, has_src, tr, Rout);
+  k_rhs_u<R, 0><<<(unsigned)((c->nf[1] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 1><<<(unsigned)((c->nf[2] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 2><<<(unsigned)((c->nf[3] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  c->launches += 3;  // launch_ok counts the fourth
   return launch_ok(c);
 }
 
@@ -1303,8 +1391,8 @@ static int rhs_impl(sph_ctx* c, Bufs<R>& b, double dt, CF<double> src, int has, 
   int e = prepare(c, b, c->iterate_set, &ub);
   if (e) return e;
   CF<double> uk = cf_of(c->iterate_set ? c->U[1 - c->cur] : c->U[c->cur]);
-  if (sizeof(R) == sizeof(double)) return run_rhs(c, b, ub, uk, dt, src, has, mf_of((R* const*)R_out));
-  e = run_rhs(c, b, ub, uk, dt, src, has, mf_of(b.Rb));
+  if (sizeof(R) == sizeof(double)) return run_rhs(c, b, ub, uk, c->iterate_set, dt, src, has, mf_of((R* const*)R_out));
+  e = run_rhs(c, b, ub, uk, c->iterate_set, dt, src, has, mf_of(b.Rb));
   if (e) return e;
   return convert_out(c, b.Rb, R_out);
 }
@@ -1355,7 +1443,7 @@ static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> s
     e = prepare(c, b, it > 0, &ub);
     if (e) break;
     CF<double> ukin = cf_of(it == 0 ? un : uk);
-    e = run_rhs(c, b, ub, ukin, dt, src, has, mf_of(b.Rb));
+    e = run_rhs(c, b, ub, ukin, it > 0, dt, src, has, mf_of(b.Rb));
     if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, ukin, mf_of(uk));
     if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, ukin, mf_of(uk));
     if (!e && it == n_iter - 1 && cudaMemsetAsync(c->acc, 0, 5 * sizeof(double), c->st) != cudaSuccess) e = SPH_ERR_CUDA;

@@ -38,12 +38,99 @@ struct Geo {
   const R* lapT;             // [nr]   (rf_{i+1}^2 (T_{i+1}-T_i) - rf_i^2 (T_i-T_{i-1})) / (rc^2 dr^2)
   const R* rhoref;           // [nr]   (p_ref + pi_inf) / (Rg T_ref)
   const R* ehyd;             // [nr+1] (p_ref[i]-p_ref[i-1]) / (dr rho_ref,f) + g on interior r-faces
+  const R* pcen;             // [nr]   p_ref + pi_inf at the centres
+  const R* Tcen;             // [nr]   T_ref at the centres
+  // rf^2 and sin(theta_f) as hi + lo pairs (lo = 0 in FP64), for div(Ubar)
+  const R *rf2h, *rf2l, *sfh, *sfl;
 };
 
 struct Par {
   double gamma, cv, Pr, mu, pinf, g, omega;
   double kappa, Rg;  // kappa = mu cp / Pr, Rg = cv (gamma-1)
+  // the same in FP32, so that FP32 kernels convert nothing from FP64
+  float gamma_f, mu_f, kappa_f, g_f, omega_f, iRg_f;
 };
+
+// a parameter in the kernel's bulk type: the FP64 value or its FP32 copy
+template <typename R> __device__ __forceinline__ R pick(double d, float) { return (R)d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// ---------------------------------------------------------------------------
+// FP64 values on the FP32 and integer pipes.  GB300 issues FP64 instructions
+// (arithmetic and conversions alike) at 1/64 of the FP32 rate, so the
+// mixed-precision kernels move values between double and float with integer
+// operations on the IEEE bit patterns, and do the few operations that need more
+// than FP32 precision in unevaluated sums of two floats (hi + lo, ~48 bits).
+
+// float -> double, exact; zero and subnormal floats give a signed zero
+__device__ __forceinline__ double f2d(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  if (e == 0) return __hiloint2double((int)sg, 0);
+  unsigned E = e == 0xffu ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
+  return __hiloint2double((int)(sg | (E << 20) | (m >> 3)), (int)(m << 29));
+}
+__device__ __forceinline__ double f2d(double d) { return d; }
+
+// 2^k as a float for -126 <= k <= 127 (zero below)
+__device__ __forceinline__ float pow2f(int k) { return k < -126 ? 0.f : __int_as_float((k + 127) << 23); }
+
+// double -> hi + lo: hi = d rounded to nearest float (ties to even), lo = the
+// remainder d - hi rounded to float.  NaN -> NaN, beyond the float range ->
+// +-inf, below 2^-126 -> +-0; lo is dropped where it would be below 2^-126.
+__device__ __forceinline__ void d2ff(double d, float& hi, float& lo) {
+  unsigned H = (unsigned)__double2hiint(d), L = (unsigned)__double2loint(d);
+  unsigned sg = H & 0x80000000u;
+  int E = (int)((H >> 20) & 0x7ffu);
+  lo = 0.f;
+  if (E == 0x7ff) { hi = __uint_as_float(sg | 0x7f800000u | (((H & 0xfffffu) | L) ? 0x400000u : 0u)); return; }
+  int e = E - 896;
+  if (e >= 255) { hi = __uint_as_float(sg | 0x7f800000u); return; }
+  if (e <= 0) { hi = __uint_as_float(sg); return; }
+  unsigned m = ((H & 0xfffffu) << 3) | (L >> 29);
+  unsigned r = L & 0x1fffffffu;
+  unsigned up = (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  hi = __uint_as_float((sg | ((unsigned)e << 23) | m) + up);  // a carry moves into the exponent
+  int rem = (int)r - (up ? 0x20000000 : 0);                    // in units of 2^(E-1075)
+  float lv = (float)rem * pow2f(E - 1075);
+  lo = sg ? -lv : lv;
+}
+// the nearest float of a double
+__device__ __forceinline__ float d2f(double d) { float h, l; d2ff(d, h, l); return h; }
+// a double in the bulk type R (exact for R = double)
+template <typename R> __device__ __forceinline__ R to_bulk(double d) { return (R)d; }
+template <> __device__ __forceinline__ float to_bulk<float>(double d) { return d2f(d); }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// a pair (hi, lo) with |lo| <= ulp(hi)/2, from s + e
+__device__ __forceinline__ void renorm(float s, float e, float& hi, float& lo) {
+  hi = s + e;
+  lo = e - (hi - s);
+}
+// (ah + al) - (bh + bl), as a pair
+__device__ __forceinline__ void ff_sub(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  two_sum(ah, -bh, s, e);
+  renorm(s, e + (al - bl), h, l);
+}
+// (ah + al) + (bh + bl), as a pair
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& h, float& l) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  renorm(s, e + (al + bl), h, l);
+}
+// (ah + al) * (bh + bl), as a pair (error-free product of the high parts by FMA)
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  renorm(p, e, h, l);
+}
 
 template <typename R>
 struct Coef {  // per cell centre, frozen at Ubar
@@ -162,11 +249,12 @@ __device__ __forceinline__ CPt<R> load_c(const Coef<R>& c, int d, int id) {
 template <typename R>
 __device__ __forceinline__ void row_cw(const Geo<R>& g, const Par& P, const CPt<R>& q, int d, int isT, int i, int j,
                                        RowC<R>& w) {
-  R gm = (R)P.gamma, mu = (R)P.mu;
+  R gm = pick<R>(P.gamma, P.gamma_f), mu = pick<R>(P.mu, P.mu_f);
   R be = q.beta;
   R alin = isT ? (gm - R(1)) * q.Tb : gm * q.Pb;
   R visc = isT ? mu * be : mu * (gm - R(1));
-  R dif = isT ? be * (R)P.kappa : (gm - R(1)) * (R)P.kappa;
+  R kap = pick<R>(P.kappa, P.kappa_f);
+  R dif = isT ? be * kap : (gm - R(1)) * kap;
   R g_rr = q.grr, g_tt = q.gtt, g_pp = q.gpp;
   R tr = g_rr + g_tt + g_pp;
   R ir = g.irc[i];
@@ -248,7 +336,7 @@ __device__ __forceinline__ FPt<R> load_f(const Geo<R>& g, const Coef<R>& c, cons
 template <typename R>
 __device__ __forceinline__ void row_fw(const Geo<R>& g, const Par& P, const FPt<R>& q, int d, int i, int j, R wp[2],
                                        R wu[3]) {
-  R mu = (R)P.mu;
+  R mu = pick<R>(P.mu, P.mu_f);
   R irh = sdiv(R(2), q.rho0 + q.rho1);
   if (d == 0) {
     R irf = g.irf[i];
@@ -311,7 +399,7 @@ __device__ __forceinline__ SPt<R> load_s(const Geo<R>& g, const Coef<R>& c, cons
 template <typename R>
 __device__ __forceinline__ void row_sw(const Geo<R>& g, const Par& P, const SPt<R>& q, int cc, int d, int i, int j,
                                        R w[3]) {
-  R mu = (R)P.mu;
+  R mu = pick<R>(P.mu, P.mu_f);
   R irh = sdiv(R(2), q.rho0 + q.rho1);
   R ir = cc == 0 ? g.irf[i] : g.irc[i];
   R is = cc == 1 ? g.isf[j] : g.isc[j];

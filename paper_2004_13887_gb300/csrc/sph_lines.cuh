@@ -221,14 +221,14 @@ __device__ __forceinline__ Group group_of(const SweepArgs<float>& S, int kind, i
   return G;
 }
 
-__device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, double* ss, int bad) {
+__device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, float* ss, int bad) {
   if (bad) atomicOr(S.flag, bad);
   if (S.update) {
 #pragma unroll
     for (int f = 0; f < 5; f++) {
-      double v = ss[f];
+      float v = ss[f];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-      if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(S.acc + f, v);
+      if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(S.acc + f, f2d(v));
     }
   }
 }
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 3 : P == 4 ? 2 : 1) k_lines
   const int n = 32 * P, cyc = (D == 2 && g.per);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float h = S.h;
-  double ss[5] = {0, 0, 0, 0, 0};
+  float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   float* slot = S.scr + ((size_t)blockIdx.x * NW + w) * (32 * slot_floats(P));
   Group G = group_of(S, 0, blockIdx.x, NW);
@@ -423,12 +423,12 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 3 : P == 4 ? 2 : 1) k_lines
     int i, j, k;
     line_pos(D, G.a, G.bb + lw, c, i, j, k);
     int ic = IC(g, i, j, k);
-    put(S, 0, ic, (double)sm[si], ss, &bad);
-    put(S, 4, ic, (double)sm[FS + si], ss, &bad);
+    put(S, 0, ic, sm[si], ss, &bad);
+    put(S, 4, ic, sm[FS + si], ss, &bad);
     int fi, fj, fk;
     next_face(D, n, c, i, j, k, fi, fj, fk);
     if (c < n - 1 || cyc) {
-      put(S, 1 + D, face_idx(g, D, fi, fj, fk), (double)sm[2 * FS + si], ss, &bad);
+      put(S, 1 + D, face_idx(g, D, fi, fj, fk), sm[2 * FS + si], ss, &bad);
     } else {
       put_wall(S, 1 + D, face_idx(g, D, fi, fj, fk));
     }
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
   const int n = 32 * P, cyc = (D == 2 && g.per);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float h = S.h;
-  double ss[5] = {0, 0, 0, 0, 0};
+  float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   Group G = group_of(S, KIND, blockIdx.x, NW);
   for (int e = threadIdx.x; e < n * NW; e += NT) {
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
     if (lw >= G.nvalid) continue;
     int i, j, k;
     line_pos(D, G.a, G.bb + lw, c, i, j, k);
-    scalar_put(S, cc, i, j, k, (double)sm[sidx<P>(lw, c)], ss, &bad);
+    scalar_put(S, cc, i, j, k, sm[sidx<P>(lw, c)], ss, &bad);
   }
   flush_norms(S, ss, bad);
 }
