@@ -97,12 +97,9 @@ __global__ void k_cvt_in(long n, const double* __restrict__ a, R* __restrict__ o
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = (R)a[t];
 }
 
-template <typename R>
-__global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int N = g.nr * g.nt * g.np;
-  if (t >= N) return;
-  int k = t % g.np, j = (t / g.np) % g.nt, i = t / (g.np * g.nt);
+template <bool CIJ, typename R>
+__device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<R>& ub, const Coef<R>& c, int i, int j,
+                                        int k, int t) {
   const R *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
   // thermodynamics from background + perturbation.  The density perturbation
   // rho - rho_ref = (p' T_ref - (p_ref + pi_inf) T') / (Rg T_ref T) has no
@@ -118,21 +115,31 @@ __global__ void k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
   c.rho[t] = pb * itb * iRg;
   c.drho[t] = sdiv((pp * Tref - pref * Tp) * itb * iRg, Tref);
   c.beta[t] = sdiv((pick<R>(P.gamma, P.gamma_f) - R(1)) * tb, pb);
-  R ur = hr(g, UR, i, j, k), ut = ht(g, UT, i, j, k), up = hp(g, UP, i, j, k);
+  R ur = hr<CIJ>(g, UR, i, j, k), ut = ht<CIJ>(g, UT, i, j, k), up = hp<CIJ>(g, UP, i, j, k);
   c.uc0[t] = ur; c.uc1[t] = ut; c.uc2[t] = up;
   R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j], h = R(0.5);
-  c.grr[t] = (vr(g, UR, i + 1, j, k) - vr(g, UR, i, j, k)) * g.idr;
-  c.gtt[t] = (vt(g, UT, i, j + 1, k) - vt(g, UT, i, j, k)) * ir * g.idth + ur * ir;
-  c.gpp[t] = (vp(g, UP, i, j, k + 1) - vp(g, UP, i, j, k)) * ir * is * g.idph + ur * ir + ut * cot * ir;
-  R grt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr;
-  R gtr = (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth - ut * ir;
-  R grp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr;
-  R gpr = (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * h * ir * is * g.idph - up * ir;
-  R gtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * h * ir * g.idth;
-  R gpt = (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * h * ir * is * g.idph - up * cot * ir;
+  c.grr[t] = (vr<CIJ>(g, UR, i + 1, j, k) - vr<CIJ>(g, UR, i, j, k)) * g.idr;
+  c.gtt[t] = (vt<CIJ>(g, UT, i, j + 1, k) - vt<CIJ>(g, UT, i, j, k)) * ir * g.idth + ur * ir;
+  c.gpp[t] = (vp<CIJ>(g, UP, i, j, k + 1) - vp<CIJ>(g, UP, i, j, k)) * ir * is * g.idph + ur * ir + ut * cot * ir;
+  R grt = (ht<CIJ>(g, UT, i + 1, j, k) - ht<CIJ>(g, UT, i - 1, j, k)) * h * g.idr;
+  R gtr = (hr<CIJ>(g, UR, i, j + 1, k) - hr<CIJ>(g, UR, i, j - 1, k)) * h * ir * g.idth - ut * ir;
+  R grp = (hp<CIJ>(g, UP, i + 1, j, k) - hp<CIJ>(g, UP, i - 1, j, k)) * h * g.idr;
+  R gpr = (hr<CIJ>(g, UR, i, j, k + 1) - hr<CIJ>(g, UR, i, j, k - 1)) * h * ir * is * g.idph - up * ir;
+  R gtp = (hp<CIJ>(g, UP, i, j + 1, k) - hp<CIJ>(g, UP, i, j - 1, k)) * h * ir * g.idth;
+  R gpt = (ht<CIJ>(g, UT, i, j, k + 1) - ht<CIJ>(g, UT, i, j, k - 1)) * h * ir * is * g.idph - up * cot * ir;
   c.srt[t] = grt + gtr;
   c.srp[t] = grp + gpr;
   c.stp[t] = gtp + gpt;
+}
+
+// one block per (i, j) row of 128 phi-consecutive centres
+template <typename R>
+__global__ void __launch_bounds__(128) k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= g.np) return;
+  int t = IC(g, i, j, k);
+  if (inner_ij(g, i, j)) coef_at<false>(g, P, ub, c, i, j, k, t);
+  else coef_at<true>(g, P, ub, c, i, j, k, t);
 }
 
 // div(Ubar) at centre (i,j,k), in FP64 from U^n and U^k (Ubar = (U^n+U^k)/2).
@@ -183,14 +190,11 @@ __device__ __forceinline__ float div_ubar_ff(const Geo<float>& g, const CF<float
 }
 
 // R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per centre.
-template <typename R>
-__global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
-                                               CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
-                                               int has_src, R tau, MF<R> Rout) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int N = g.nr * g.nt * g.np;
-  if (t >= N) return;
-  int k = t % g.np, j = (t / g.np) % g.nt, i = t / (g.np * g.nt);
+template <bool CIJ, typename R>
+__device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd, const Par& P, const Coef<R>& c,
+                                         const CF<R>& ub, const CF<R>& ul, const CF<double>& un, const CF<double>& uk,
+                                         const CF<R>& D, int hasD, const CF<double>& src, int has_src, R tau,
+                                         const MF<R>& Rout, int i, int j, int k, int t) {
   const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
   R mu = pick<R>(P.mu, P.mu_f), gm = pick<R>(P.gamma, P.gamma_f), h = R(0.5);
   R ir = g.irc[i], is = g.isc[j];
@@ -202,12 +206,12 @@ __global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, 
     R pv[3], Tv[3], uv[2];
 #pragma unroll
     for (int s = -1; s <= 1; s++) {
-      pv[s + 1] = cpert(g, Pp, i + s * di, j + s * dj, k + s * dk);
-      Tv[s + 1] = cpert(g, TT, i + s * di, j + s * dj, k + s * dk);
+      pv[s + 1] = cpert<CIJ>(g, Pp, i + s * di, j + s * dj, k + s * dk);
+      Tv[s + 1] = cpert<CIJ>(g, TT, i + s * di, j + s * dj, k + s * dk);
     }
     if (d == 0) { uv[0] = UR[IRf(g, i, j, k)]; uv[1] = UR[IRf(g, i + 1, j, k)]; }
     else if (d == 1) { uv[0] = UT[ITf(g, i, j, k)]; uv[1] = UT[ITf(g, i, j + 1, k)]; }
-    else { uv[0] = vp(g, UP, i, j, k); uv[1] = vp(g, UP, i, j, k + 1); }
+    else { uv[0] = vp<CIJ>(g, UP, i, j, k); uv[1] = vp<CIJ>(g, UP, i, j, k + 1); }
     RowC<R> w;
     row_c(g, P, c, d, 0, i, j, k, w);
     accp += w.wp[0] * pv[0] + w.wp[2] * pv[2] + w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2]
@@ -222,12 +226,12 @@ __global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, 
   R divu;
   if constexpr (sizeof(R) == sizeof(double)) divu = div_ubar(gd, un, uk, i, j, k);
   else divu = div_ubar_ff(g, ub, ul, i, j, k);
-  R xrt = (ht(g, UT, i + 1, j, k) - ht(g, UT, i - 1, j, k)) * h * g.idr
-        + (hr(g, UR, i, j + 1, k) - hr(g, UR, i, j - 1, k)) * h * ir * g.idth;
-  R xrp = (hp(g, UP, i + 1, j, k) - hp(g, UP, i - 1, j, k)) * h * g.idr
-        + (hr(g, UR, i, j, k + 1) - hr(g, UR, i, j, k - 1)) * h * ir * is * g.idph;
-  R xtp = (hp(g, UP, i, j + 1, k) - hp(g, UP, i, j - 1, k)) * h * ir * g.idth
-        + (ht(g, UT, i, j, k + 1) - ht(g, UT, i, j, k - 1)) * h * ir * is * g.idph;
+  R xrt = (ht<CIJ>(g, UT, i + 1, j, k) - ht<CIJ>(g, UT, i - 1, j, k)) * h * g.idr
+        + (hr<CIJ>(g, UR, i, j + 1, k) - hr<CIJ>(g, UR, i, j - 1, k)) * h * ir * g.idth;
+  R xrp = (hp<CIJ>(g, UP, i + 1, j, k) - hp<CIJ>(g, UP, i - 1, j, k)) * h * g.idr
+        + (hr<CIJ>(g, UR, i, j, k + 1) - hr<CIJ>(g, UR, i, j, k - 1)) * h * ir * is * g.idph;
+  R xtp = (hp<CIJ>(g, UP, i, j + 1, k) - hp<CIJ>(g, UP, i, j - 1, k)) * h * ir * g.idth
+        + (ht<CIJ>(g, UT, i, j, k + 1) - ht<CIJ>(g, UT, i, j, k - 1)) * h * ir * is * g.idph;
   R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
   accp += -mu * (gm - R(1)) * cross;
   accT += -mu * c.beta[t] * cross;
@@ -238,29 +242,36 @@ __global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, 
   Rout.f[4][t] = -d4 - tau * NT;
 }
 
+// one block per (i, j) row of 128 phi-consecutive centres
+template <typename R>
+__global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
+                                               CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
+                                               int has_src, R tau, MF<R> Rout) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= g.np) return;
+  int t = IC(g, i, j, k);
+  if (inner_ij(g, i, j)) rhs_c_at<false>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+  else rhs_c_at<true>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+}
+
 // R for the momentum row of component D on its faces: one thread per face
 // (zero on wall faces, which are not unknowns).
-template <typename R, int D>
-__global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<R> Dv, int hasD,
-                                               CF<double> src, int has_src, R tau, MF<R> Rout) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int ni = g.nr + (D == 0), nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
-  if (t >= ni * nj * nk) return;
-  int k = t % nk, j = (t / nk) % nj, i = t / (nk * nj);
-  bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
-  if (wall) { Rout.f[1 + D][t] = R(0); return; }
+template <bool CIJ, int D, typename R>
+__device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub,
+                                         const CF<R>& Dv, int hasD, const CF<double>& src, int has_src, R tau,
+                                         const MF<R>& Rout, int i, int j, int k, int t) {
   const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
   R mu = pick<R>(P.mu, P.mu_f), om = pick<R>(P.omega, P.omega_f), h = R(0.5);
   R wp[2], wu[3], w[3];
   R acc;
   if (D == 0) {
     row_f(g, P, c, UR, 0, i, j, k, wp, wu);
-    acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i - 1, j, k))
+    acc = wp[1] * (cpert<CIJ>(g, Pp, i, j, k) - cpert<CIJ>(g, Pp, i - 1, j, k))
         + wu[0] * UR[IRf(g, i - 1, j, k)] + wu[1] * UR[t] + wu[2] * UR[IRf(g, i + 1, j, k)];
-    row_s(g, P, c, ub, 0, 1, i, j, k, w);
-    acc += w[0] * vr(g, UR, i, j - 1, k) + w[1] * UR[t] + w[2] * vr(g, UR, i, j + 1, k);
-    row_s(g, P, c, ub, 0, 2, i, j, k, w);
-    acc += w[0] * vr(g, UR, i, j, k - 1) + w[1] * UR[t] + w[2] * vr(g, UR, i, j, k + 1);
+    row_s<CIJ>(g, P, c, ub, 0, 1, i, j, k, w);
+    acc += w[0] * vr<CIJ>(g, UR, i, j - 1, k) + w[1] * UR[t] + w[2] * vr<CIJ>(g, UR, i, j + 1, k);
+    row_s<CIJ>(g, P, c, ub, 0, 2, i, j, k, w);
+    acc += w[0] * vr<CIJ>(g, UR, i, j, k - 1) + w[1] * UR[t] + w[2] * vr<CIJ>(g, UR, i, j, k + 1);
     // hydrostatic part: (1/rho_f) d p_ref/dr + g = (1 - b) e + g b, b = 1 - rho_ref,f / rho_f
     int c0 = IC(g, i - 1, j, k), c1 = IC(g, i, j, k);
     R rs = c.rho[c0] + c.rho[c1];
@@ -269,75 +280,90 @@ __global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R>
     // D_M
     R irf = g.irf[i], s = g.sc[j], is = g.isc[j];
     R irh = sdiv(R(2), rs);
-    R utf = h * (ht(g, UT, i - 1, j, k) + ht(g, UT, i, j, k));
-    R upf = h * (hp(g, UP, i - 1, j, k) + hp(g, UP, i, j, k));
+    R utf = h * (ht<CIJ>(g, UT, i - 1, j, k) + ht<CIJ>(g, UT, i, j, k));
+    R upf = h * (hp<CIJ>(g, UP, i - 1, j, k) + hp<CIJ>(g, UP, i, j, k));
     R Q[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = i - 1 + q;
       Q[q] = (g.sf[j + 1] * UT[ITf(g, m, j + 1, k)] - g.sf[j] * UT[ITf(g, m, j, k)]) * g.irc[m] * is * g.idth
-           + (vp(g, UP, m, j, k + 1) - vp(g, UP, m, j, k)) * g.irc[m] * is * g.idph;
+           + (vp<CIJ>(g, UP, m, j, k + 1) - vp<CIJ>(g, UP, m, j, k)) * g.irc[m] * is * g.idph;
     }
     acc += -utf * utf * irf - upf * upf * irf + R(2) * mu * irh * UR[t] * irf * irf - R(2) * om * s * upf
          - mu * irh * R(1.0 / 3.0) * g.idr * (Q[1] - Q[0]) + mu * irh * irf * (Q[0] + Q[1]);
   } else if (D == 1) {
     R ir = g.irc[i];
     row_f(g, P, c, UT, 1, i, j, k, wp, wu);
-    acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j - 1, k))
+    acc = wp[1] * (cpert<CIJ>(g, Pp, i, j, k) - cpert<CIJ>(g, Pp, i, j - 1, k))
         + wu[0] * UT[ITf(g, i, j - 1, k)] + wu[1] * UT[t] + wu[2] * UT[ITf(g, i, j + 1, k)];
-    row_s(g, P, c, ub, 1, 0, i, j, k, w);
-    acc += w[0] * vt(g, UT, i - 1, j, k) + w[1] * UT[t] + w[2] * vt(g, UT, i + 1, j, k);
-    row_s(g, P, c, ub, 1, 2, i, j, k, w);
-    acc += w[0] * vt(g, UT, i, j, k - 1) + w[1] * UT[t] + w[2] * vt(g, UT, i, j, k + 1);
+    row_s<CIJ>(g, P, c, ub, 1, 0, i, j, k, w);
+    acc += w[0] * vt<CIJ>(g, UT, i - 1, j, k) + w[1] * UT[t] + w[2] * vt<CIJ>(g, UT, i + 1, j, k);
+    row_s<CIJ>(g, P, c, ub, 1, 2, i, j, k, w);
+    acc += w[0] * vt<CIJ>(g, UT, i, j, k - 1) + w[1] * UT[t] + w[2] * vt<CIJ>(g, UT, i, j, k + 1);
     R isfj = g.isf[j], cfj = g.cf[j], cotf = g.cotf[j];
     R irh = sdiv(R(2), rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
     R ubt = UT[t];
-    R upf = h * (hp(g, UP, i, j - 1, k) + hp(g, UP, i, j, k));
-    R vrf = h * (hr(g, UR, i, j - 1, k) + hr(g, UR, i, j, k));
+    R upf = h * (hp<CIJ>(g, UP, i, j - 1, k) + hp<CIJ>(g, UP, i, j, k));
+    R vrf = h * (hr<CIJ>(g, UR, i, j - 1, k) + hr<CIJ>(g, UR, i, j, k));
     R Dr[2], Dp[2], dpf = R(0);
 #pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = j - 1 + q;
       Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * UR[IRf(g, i + 1, m, k)] - g.rf[i] * g.rf[i] * UR[IRf(g, i, m, k)])
             * ir * ir * g.idr;
-      R dv = vp(g, UP, i, m, k + 1) - vp(g, UP, i, m, k);
+      R dv = vp<CIJ>(g, UP, i, m, k + 1) - vp<CIJ>(g, UP, i, m, k);
       Dp[q] = dv * ir * g.isc[m] * g.idph;
       dpf += h * dv * g.idph;
     }
     acc += ubt * vrf * ir - upf * upf * cotf * ir + mu * irh * ubt * ir * ir * isfj * isfj - R(2) * om * cfj * upf
          - mu * irh * R(1.0 / 3.0) * ir * g.idth * ((Dr[1] - Dr[0]) + (Dp[1] - Dp[0]))
-         - mu * irh * (R(2) * ir * ir * g.idth * (hr(g, UR, i, j, k) - hr(g, UR, i, j - 1, k))
+         - mu * irh * (R(2) * ir * ir * g.idth * (hr<CIJ>(g, UR, i, j, k) - hr<CIJ>(g, UR, i, j - 1, k))
                        - R(2) * cfj * ir * ir * isfj * isfj * dpf);
   } else {
     R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
     row_f(g, P, c, UP, 2, i, j, k, wp, wu);
-    acc = wp[1] * (cpert(g, Pp, i, j, k) - cpert(g, Pp, i, j, k - 1))
-        + wu[0] * vp(g, UP, i, j, k - 1) + wu[1] * UP[t] + wu[2] * vp(g, UP, i, j, k + 1);
-    row_s(g, P, c, ub, 2, 0, i, j, k, w);
-    acc += w[0] * vp(g, UP, i - 1, j, k) + w[1] * UP[t] + w[2] * vp(g, UP, i + 1, j, k);
-    row_s(g, P, c, ub, 2, 1, i, j, k, w);
-    acc += w[0] * vp(g, UP, i, j - 1, k) + w[1] * UP[t] + w[2] * vp(g, UP, i, j + 1, k);
+    acc = wp[1] * (cpert<CIJ>(g, Pp, i, j, k) - cpert<CIJ>(g, Pp, i, j, k - 1))
+        + wu[0] * vp<CIJ>(g, UP, i, j, k - 1) + wu[1] * UP[t] + wu[2] * vp<CIJ>(g, UP, i, j, k + 1);
+    row_s<CIJ>(g, P, c, ub, 2, 0, i, j, k, w);
+    acc += w[0] * vp<CIJ>(g, UP, i - 1, j, k) + w[1] * UP[t] + w[2] * vp<CIJ>(g, UP, i + 1, j, k);
+    row_s<CIJ>(g, P, c, ub, 2, 1, i, j, k, w);
+    acc += w[0] * vp<CIJ>(g, UP, i, j - 1, k) + w[1] * UP[t] + w[2] * vp<CIJ>(g, UP, i, j + 1, k);
     R s = g.sc[j], cj = g.cc[j];
     R irh = sdiv(R(2), rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
     R ubp = UP[t];
-    R vrf = h * (hr(g, UR, i, j, k - 1) + hr(g, UR, i, j, k));
-    R vtf = h * (ht(g, UT, i, j, k - 1) + ht(g, UT, i, j, k));
+    R vrf = h * (hr<CIJ>(g, UR, i, j, k - 1) + hr<CIJ>(g, UR, i, j, k));
+    R vtf = h * (ht<CIJ>(g, UT, i, j, k - 1) + ht<CIJ>(g, UT, i, j, k));
     R Dr[2], Dt[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = k - 1 + q;
-      Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * vr(g, UR, i + 1, j, m) - g.rf[i] * g.rf[i] * vr(g, UR, i, j, m))
+      Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * vr<CIJ>(g, UR, i + 1, j, m) - g.rf[i] * g.rf[i] * vr<CIJ>(g, UR, i, j, m))
             * ir * ir * g.idr;
-      Dt[q] = (g.sf[j + 1] * vt(g, UT, i, j + 1, m) - g.sf[j] * vt(g, UT, i, j, m)) * ir * is * g.idth;
+      Dt[q] = (g.sf[j + 1] * vt<CIJ>(g, UT, i, j + 1, m) - g.sf[j] * vt<CIJ>(g, UT, i, j, m)) * ir * is * g.idth;
     }
     acc += ubp * vtf * cot * ir + ubp * vrf * ir + mu * irh * ubp * ir * ir * is * is + R(2) * om * (cj * vtf + s * vrf)
          - mu * irh * R(1.0 / 3.0) * ir * is * g.idph * ((Dr[1] - Dr[0]) + (Dt[1] - Dt[0]))
-         - mu * irh * (R(2) * ir * ir * is * g.idph * (hr(g, UR, i, j, k) - hr(g, UR, i, j, k - 1))
-                       + R(2) * cj * ir * ir * is * is * g.idph * (ht(g, UT, i, j, k) - ht(g, UT, i, j, k - 1)));
+         - mu * irh * (R(2) * ir * ir * is * g.idph * (hr<CIJ>(g, UR, i, j, k) - hr<CIJ>(g, UR, i, j, k - 1))
+                       + R(2) * cj * ir * ir * is * is * g.idph * (ht<CIJ>(g, UT, i, j, k) - ht<CIJ>(g, UT, i, j, k - 1)));
   }
   if (has_src) acc -= to_bulk<R>(src.f[1 + D][t]);
   R dd = hasD ? Dv.f[1 + D][t] : R(0);
   Rout.f[1 + D][t] = -dd - tau * acc;
+}
+
+// one block per (i, j) row of 128 phi-consecutive faces; zero on wall faces,
+// which are not unknowns
+template <typename R, int D>
+__global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<R> Dv, int hasD,
+                                               CF<double> src, int has_src, R tau, MF<R> Rout) {
+  int nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
+  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k >= nk) return;
+  int t = (i * nj + j) * nk + k;
+  bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
+  if (wall) { Rout.f[1 + D][t] = R(0); return; }
+  if (inner_ij(g, i, j)) rhs_u_at<false, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+  else rhs_u_at<true, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
 }
 
 // ------------------------------------------------------------ line solvers
@@ -1202,7 +1228,8 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
     ub = cf_of(b.Ub);
   }
   k_begin(c, SPH_K_COEF);
-  k_coef<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->P, ub, b.c);
+  const Geo<double>& gg = c->d64.g;
+  k_coef<R><<<dim3((gg.np + 127) / 128, gg.nt, gg.nr), 128, 0, c->st>>>(b.g, c->P, ub, b.c);
   if (launch_ok(c)) return SPH_ERR_CUDA;
   *ub_out = ub;
   return SPH_OK;
@@ -1218,11 +1245,13 @@ static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, do
   CF<R> ul = sizeof(R) == sizeof(float) ? cf_of(b.UbLo) : ub;  // velocity remainders of Ubar (FP32 mode)
   R tr = (R)tau;
   k_begin(c, SPH_K_RHS);
-  k_rhs_c<R><<<(unsigned)((c->N + 127) / 128), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD,
-                                                                  src, has_src, tr, Rout);
-  k_rhs_u<R, 0><<<(unsigned)((c->nf[1] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 1><<<(unsigned)((c->nf[2] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 2><<<(unsigned)((c->nf[3] + 127) / 128), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  const Geo<double>& gg = c->d64.g;
+  int nr = gg.nr, nt = gg.nt, np = gg.np, npf = gg.npf;
+  k_rhs_c<R><<<dim3((np + 127) / 128, nt, nr), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD, src,
+                                                                has_src, tr, Rout);
+  k_rhs_u<R, 0><<<dim3((np + 127) / 128, nt, nr + 1), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 1><<<dim3((np + 127) / 128, nt + 1, nr), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 2><<<dim3((npf + 127) / 128, nt, nr), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
   c->launches += 3;  // launch_ok counts the fourth
   return launch_ok(c);
 }

@@ -157,59 +157,69 @@ template <typename G> __device__ __forceinline__ int wrapk(const G& g, int k) { 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ---------------------------------------------------------------- accessors
+// CIJ = false skips the checks on i and j: for points whose +-2 neighbourhood in
+// r and theta is inside the grid (the kernels decide this per block, so warps
+// do not diverge); k (phi) is always checked.
+//
 // Centre perturbation with zero Neumann ghosts (the background has its own).
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R cpert(const G& g, const R* f, int i, int j, int k) {
-  int ii = clampi(i, 0, g.nr - 1), jj = clampi(j, 0, g.nt - 1);
+  int ii = CIJ ? clampi(i, 0, g.nr - 1) : i, jj = CIJ ? clampi(j, 0, g.nt - 1) : j;
   int kk = g.per ? wrapk(g, k) : clampi(k, 0, g.np - 1);
   return f[IC(g, ii, jj, kk)];
 }
 // Velocities with no-slip ghosts (ghost = -interior) on tangential walls.
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R vr(const G& g, const R* u, int i, int j, int k) {
-  if (j < 0) return -u[IRf(g, i, 0, k)];
-  if (j >= g.nt) return -u[IRf(g, i, g.nt - 1, k)];
+  if (CIJ && j < 0) return -u[IRf(g, i, 0, k)];
+  if (CIJ && j >= g.nt) return -u[IRf(g, i, g.nt - 1, k)];
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
     else return -u[IRf(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return u[IRf(g, i, j, k)];
 }
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R vt(const G& g, const R* u, int i, int j, int k) {
-  if (i < 0) return -u[ITf(g, 0, j, k)];
-  if (i >= g.nr) return -u[ITf(g, g.nr - 1, j, k)];
+  if (CIJ && i < 0) return -u[ITf(g, 0, j, k)];
+  if (CIJ && i >= g.nr) return -u[ITf(g, g.nr - 1, j, k)];
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
     else return -u[ITf(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return u[ITf(g, i, j, k)];
 }
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R vp(const G& g, const R* u, int i, int j, int k) {
   if (g.per) k = wrapk(g, k);
-  if (i < 0) return -u[IPf(g, 0, j, k)];
-  if (i >= g.nr) return -u[IPf(g, g.nr - 1, j, k)];
-  if (j < 0) return -u[IPf(g, i, 0, k)];
-  if (j >= g.nt) return -u[IPf(g, i, g.nt - 1, k)];
+  if (CIJ && i < 0) return -u[IPf(g, 0, j, k)];
+  if (CIJ && i >= g.nr) return -u[IPf(g, g.nr - 1, j, k)];
+  if (CIJ && j < 0) return -u[IPf(g, i, 0, k)];
+  if (CIJ && j >= g.nt) return -u[IPf(g, i, g.nt - 1, k)];
   return u[IPf(g, i, j, k)];
 }
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R hr(const G& g, const R* u, int i, int j, int k) {
-  return R(0.5) * (vr(g, u, i, j, k) + vr(g, u, i + 1, j, k));
+  return R(0.5) * (vr<CIJ>(g, u, i, j, k) + vr<CIJ>(g, u, i + 1, j, k));
 }
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R ht(const G& g, const R* u, int i, int j, int k) {
-  return R(0.5) * (vt(g, u, i, j, k) + vt(g, u, i, j + 1, k));
+  return R(0.5) * (vt<CIJ>(g, u, i, j, k) + vt<CIJ>(g, u, i, j + 1, k));
 }
-template <typename G, typename R>
+template <bool CIJ = true, typename G, typename R>
 __device__ __forceinline__ R hp(const G& g, const R* u, int i, int j, int k) {
-  return R(0.5) * (vp(g, u, i, j, k) + vp(g, u, i, j, k + 1));
+  return R(0.5) * (vp<CIJ>(g, u, i, j, k) + vp<CIJ>(g, u, i, j, k + 1));
 }
 template <typename R>
 __device__ __forceinline__ R rho_at(const Geo<R>& g, const Coef<R>& c, int i, int j, int k) {
   if (g.per) k = wrapk(g, k);
   return c.rho[IC(g, i, j, k)];
+}
+
+// whether the +-2 neighbourhood of (i, j) in r and theta is inside the grid
+template <typename G>
+__device__ __forceinline__ bool inner_ij(const G& g, int i, int j) {
+  return i >= 2 && i <= g.nr - 3 && j >= 2 && j <= g.nt - 3;
 }
 
 // ------------------------------------------------------------------- rows
@@ -380,19 +390,19 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
 template <typename R>
 struct SPt { R rho0, rho1, ua; };
 
-template <typename R>
+template <bool CIJ = true, typename R>
 __device__ __forceinline__ SPt<R> load_s(const Geo<R>& g, const Coef<R>& c, const CF<R>& ub, int cc, int d, int i,
                                          int j, int k) {
   SPt<R> q;
   if (cc == 0) { q.rho0 = rho_at(g, c, i - 1, j, k); q.rho1 = rho_at(g, c, i, j, k); }
   else if (cc == 1) { q.rho0 = rho_at(g, c, i, j - 1, k); q.rho1 = rho_at(g, c, i, j, k); }
   else { q.rho0 = rho_at(g, c, i, j, k - 1); q.rho1 = rho_at(g, c, i, j, k); }
-  if (cc == 0) q.ua = d == 1 ? R(0.5) * (ht(g, ub.f[2], i - 1, j, k) + ht(g, ub.f[2], i, j, k))
-                             : R(0.5) * (hp(g, ub.f[3], i - 1, j, k) + hp(g, ub.f[3], i, j, k));
-  else if (cc == 1) q.ua = d == 0 ? R(0.5) * (hr(g, ub.f[1], i, j - 1, k) + hr(g, ub.f[1], i, j, k))
-                                  : R(0.5) * (hp(g, ub.f[3], i, j - 1, k) + hp(g, ub.f[3], i, j, k));
-  else q.ua = d == 0 ? R(0.5) * (hr(g, ub.f[1], i, j, k - 1) + hr(g, ub.f[1], i, j, k))
-                     : R(0.5) * (ht(g, ub.f[2], i, j, k - 1) + ht(g, ub.f[2], i, j, k));
+  if (cc == 0) q.ua = d == 1 ? R(0.5) * (ht<CIJ>(g, ub.f[2], i - 1, j, k) + ht<CIJ>(g, ub.f[2], i, j, k))
+                             : R(0.5) * (hp<CIJ>(g, ub.f[3], i - 1, j, k) + hp<CIJ>(g, ub.f[3], i, j, k));
+  else if (cc == 1) q.ua = d == 0 ? R(0.5) * (hr<CIJ>(g, ub.f[1], i, j - 1, k) + hr<CIJ>(g, ub.f[1], i, j, k))
+                                  : R(0.5) * (hp<CIJ>(g, ub.f[3], i, j - 1, k) + hp<CIJ>(g, ub.f[3], i, j, k));
+  else q.ua = d == 0 ? R(0.5) * (hr<CIJ>(g, ub.f[1], i, j, k - 1) + hr<CIJ>(g, ub.f[1], i, j, k))
+                     : R(0.5) * (ht<CIJ>(g, ub.f[2], i, j, k - 1) + ht<CIJ>(g, ub.f[2], i, j, k));
   return q;
 }
 
@@ -418,10 +428,10 @@ __device__ __forceinline__ void row_sw(const Geo<R>& g, const Par& P, const SPt<
   }
 }
 
-template <typename R>
+template <bool CIJ = true, typename R>
 __device__ __forceinline__ void row_s(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int cc, int d,
                                       int i, int j, int k, R w[3]) {
-  row_sw(g, P, load_s(g, c, ub, cc, d, i, j, k), cc, d, i, j, w);
+  row_sw(g, P, load_s<CIJ>(g, c, ub, cc, d, i, j, k), cc, d, i, j, w);
 }
 
 }  // namespace sph
