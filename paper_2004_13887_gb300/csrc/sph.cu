@@ -483,11 +483,19 @@ __device__ __forceinline__ void put(const SweepArgs<R>& A, int f, int idx, V v, 
     A.x.f[f][idx] = (R)v;
   } else {
     double nv = A.base.f[f][idx] + f2d(v);
-    if (!isfinite(nv)) *bad |= FLAG_NONFINITE;
+    if (!isfinite(v)) *bad |= FLAG_NONFINITE;  // the state was finite; only a non-finite increment spoils it
     A.uk.f[f][idx] = nv;
     R r = (R)v;
     ss[f] += r * r;
   }
+}
+// the update-mode store with the FP64 state value already loaded
+template <typename R, typename V>
+__device__ __forceinline__ void put_upd(const SweepArgs<R>& A, int f, int idx, double base, V v, R* ss, int* bad) {
+  if (!isfinite(v)) *bad |= FLAG_NONFINITE;
+  A.uk.f[f][idx] = base + f2d(v);
+  R r = (R)v;
+  ss[f] += r * r;
 }
 // wall face of field f: x = 0, or uk = base (mode 1)
 template <typename R>
@@ -650,12 +658,10 @@ __host__ __device__ constexpr int trans_comp(int d, int kind) {
   return d == 0 ? (kind == 1 ? 1 : 2) : d == 1 ? (kind == 1 ? 0 : 2) : (kind == 1 ? 0 : 1);
 }
 
-// output of a transverse line value at cell m, plus the wall faces of that
-// component next to the first / last line
-template <typename R, typename V>
-__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, V v, R* ss, int* bad) {
+// the wall faces of component cc next to the first / last transverse line
+template <typename R>
+__device__ __forceinline__ void scalar_walls(const SweepArgs<R>& S, int cc, int i, int j, int k) {
   const Geo<R>& g = S.g;
-  put(S, 1 + cc, face_idx(g, cc, i, j, k), v, ss, bad);
   int lo = (cc == 0) ? (i == 1) : (cc == 1) ? (j == 1) : (k == 1);
   int hi = (cc == 0) ? (i == g.nr - 1) : (cc == 1) ? (j == g.nt - 1) : (k == g.np - 1);
   if (cc == 2 && g.per) lo = hi = 0;
@@ -669,6 +675,14 @@ __device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i,
     if (cc == 0) wi = g.nr; else if (cc == 1) wj = g.nt; else wk = g.np;
     put_wall(S, 1 + cc, face_idx(g, cc, wi, wj, wk));
   }
+}
+
+// output of a transverse line value at cell m, plus the wall faces of that
+// component next to the first / last line
+template <typename R, typename V>
+__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, V v, R* ss, int* bad) {
+  put(S, 1 + cc, face_idx(S.g, cc, i, j, k), v, ss, bad);
+  scalar_walls(S, cc, i, j, k);
 }
 
 template <typename R, int D, int KIND>

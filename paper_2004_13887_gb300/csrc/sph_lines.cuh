@@ -172,28 +172,49 @@ __device__ __forceinline__ float pcr1(float a, float c, float r, int lane, int c
 
 // ------------------------------------------------------------------ staging
 
-// stage the inputs of block-line cell c of line (a, b) at shared index si
+// 4-byte asynchronous copy global -> shared (no register holds the value, so a
+// thread keeps all its staging copies in flight at once)
+__device__ __forceinline__ void cpa4(float* dst, const float* src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// stage the inputs of block-line cell c of line (a, b) at shared index si:
+// the centre coefficients, rho on both sides of face c+1, Ubar's u_D there and
+// the three right-hand-side values (a line's last face of a walled line has no
+// row: constants)
 template <int D>
 __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c, int n,
                                             int cyc) {
   const Geo<float>& g = S.g;
+  const Coef<float>& C = S.c;
   int i, j, k;
   line_pos(D, a, b, c, i, j, k);
   int ic = IC(g, i, j, k);
-  CPt<float> q = load_c(S.c, D, ic);
-  sm[0 * FS + si] = q.Pb; sm[1 * FS + si] = q.Tb; sm[2 * FS + si] = q.beta; sm[3 * FS + si] = q.uc;
-  sm[4 * FS + si] = q.grr; sm[5 * FS + si] = q.gtt; sm[6 * FS + si] = q.gpp;
-  if (D > 0) { sm[7 * FS + si] = q.s1; sm[8 * FS + si] = q.s2; }
-  FPt<float> f = {1.f, 1.f, 0.f};
-  float ru = 0.f;
+  cpa4(sm + 0 * FS + si, C.Pb + ic); cpa4(sm + 1 * FS + si, C.Tb + ic); cpa4(sm + 2 * FS + si, C.beta + ic);
+  cpa4(sm + 3 * FS + si, (D == 0 ? C.uc0 : D == 1 ? C.uc1 : C.uc2) + ic);
+  cpa4(sm + 4 * FS + si, C.grr + ic); cpa4(sm + 5 * FS + si, C.gtt + ic); cpa4(sm + 6 * FS + si, C.gpp + ic);
+  if (D == 1) { cpa4(sm + 7 * FS + si, C.srt + ic); sm[8 * FS + si] = 0.f; }
+  if (D == 2) { cpa4(sm + 7 * FS + si, C.srp + ic); cpa4(sm + 8 * FS + si, C.stp + ic); }
   if (c < n - 1 || cyc) {
     int fi, fj, fk;
     next_face(D, n, c, i, j, k, fi, fj, fk);
-    f = load_f(g, S.c, S.ub.f[1 + D], D, fi, fj, fk);
-    ru = S.rhs.f[1 + D][face_idx(g, D, fi, fj, fk)];
+    int f = face_idx(g, D, fi, fj, fk);
+    // rho at the centres on both sides of the face (the cell and the next one along D)
+    int in = D == 0 ? IC(g, fi, j, k) : D == 1 ? IC(g, i, fj, k) : IC(g, i, j, fk);
+    cpa4(sm + 9 * FS + si, C.rho + ic);
+    cpa4(sm + 10 * FS + si, C.rho + in);
+    cpa4(sm + 11 * FS + si, S.ub.f[1 + D] + f);
+    cpa4(sm + 14 * FS + si, S.rhs.f[1 + D] + f);
+  } else {
+    sm[9 * FS + si] = 1.f; sm[10 * FS + si] = 1.f; sm[11 * FS + si] = 0.f; sm[14 * FS + si] = 0.f;
   }
-  sm[9 * FS + si] = f.rho0; sm[10 * FS + si] = f.rho1; sm[11 * FS + si] = f.ub;
-  sm[12 * FS + si] = S.rhs.f[0][ic]; sm[13 * FS + si] = S.rhs.f[4][ic]; sm[14 * FS + si] = ru;
+  cpa4(sm + 12 * FS + si, S.rhs.f[0] + ic);
+  cpa4(sm + 13 * FS + si, S.rhs.f[4] + ic);
 }
 
 // stage the inputs of scalar-line cell c (component cc) of line (a, b)
@@ -250,12 +271,14 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 3 : P == 4 ? 2 : 1) k_lines
   int bad = 0;
   float* slot = S.scr + ((size_t)blockIdx.x * NW + w) * (32 * slot_floats(P));
   Group G = group_of(S, 0, blockIdx.x, NW);
-  // 1. stage
-  for (int e = threadIdx.x; e < n * NW; e += NT) {
+  // 1. stage (n NW = P NT elements: P per thread, all copies in flight)
+#pragma unroll
+  for (int q = 0; q < P; q++) {
     int lw, c;
-    elem<D, P>(e, lw, c);
+    elem<D, P>(threadIdx.x + q * NT, lw, c);
     if (lw < G.nvalid) stage_block<D>(S, sm, sidx<P>(lw, c), G.a, G.bb + lw, c, n, cyc);
   }
+  cpa_wait_all();
   __syncthreads();
   if (w < G.nvalid) {
     // 2. chunk elimination; the slot holds (E, g, H) of each interior cell, lane-interleaved
@@ -414,28 +437,67 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 3 : P == 4 ? 2 : 1) k_lines
     }
   }
   __syncthreads();
-  // 5. write back (coalesced like the staging)
-  for (int e = threadIdx.x; e < n * NW; e += NT) {
-    int lw, c;
-    elem<D, P>(e, lw, c);
-    if (lw >= G.nvalid) continue;
-    int si = sidx<P>(lw, c);
-    int i, j, k;
-    line_pos(D, G.a, G.bb + lw, c, i, j, k);
-    int ic = IC(g, i, j, k);
-    put(S, 0, ic, sm[si], ss, &bad);
-    put(S, 4, ic, sm[FS + si], ss, &bad);
-    int fi, fj, fk;
-    next_face(D, n, c, i, j, k, fi, fj, fk);
-    if (c < n - 1 || cyc) {
-      put(S, 1 + D, face_idx(g, D, fi, fj, fk), sm[2 * FS + si], ss, &bad);
-    } else {
-      put_wall(S, 1 + D, face_idx(g, D, fi, fj, fk));
+  // 5. write back (coalesced like the staging).  In update mode every FP64
+  // state value a thread needs is loaded before any store, so the loads are in
+  // flight together (the compiler may not move a load above a possibly
+  // aliasing store).
+  if (!S.update) {
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+      int lw, c;
+      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      if (lw >= G.nvalid) continue;
+      int si = sidx<P>(lw, c);
+      int i, j, k;
+      line_pos(D, G.a, G.bb + lw, c, i, j, k);
+      int ic = IC(g, i, j, k);
+      S.x.f[0][ic] = sm[si];
+      S.x.f[4][ic] = sm[FS + si];
+      int fi, fj, fk;
+      next_face(D, n, c, i, j, k, fi, fj, fk);
+      S.x.f[1 + D][face_idx(g, D, fi, fj, fk)] = (c < n - 1 || cyc) ? sm[2 * FS + si] : 0.f;
+      if (c == 0 && !cyc) {
+        int wi = i, wj = j, wk = k;
+        if (D == 0) wi = 0; else if (D == 1) wj = 0; else wk = 0;
+        S.x.f[1 + D][face_idx(g, D, wi, wj, wk)] = 0.f;
+      }
     }
-    if (c == 0 && !cyc) {
-      int wi = i, wj = j, wk = k;
-      if (D == 0) wi = 0; else if (D == 1) wj = 0; else wk = 0;
-      put_wall(S, 1 + D, face_idx(g, D, wi, wj, wk));
+  } else {
+    int ic[P], iu[P], iw[P];
+    double bp[P], bT[P], bu[P], bw[P];
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+      int lw, c;
+      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      ic[q] = iu[q] = iw[q] = -1;
+      if (lw >= G.nvalid) continue;
+      int i, j, k;
+      line_pos(D, G.a, G.bb + lw, c, i, j, k);
+      ic[q] = IC(g, i, j, k);
+      int fi, fj, fk;
+      next_face(D, n, c, i, j, k, fi, fj, fk);
+      iu[q] = face_idx(g, D, fi, fj, fk);
+      if (c == 0 && !cyc) {
+        int wi = i, wj = j, wk = k;
+        if (D == 0) wi = 0; else if (D == 1) wj = 0; else wk = 0;
+        iw[q] = face_idx(g, D, wi, wj, wk);
+      }
+      bp[q] = S.base.f[0][ic[q]];
+      bT[q] = S.base.f[4][ic[q]];
+      bu[q] = S.base.f[1 + D][iu[q]];
+      bw[q] = iw[q] >= 0 ? S.base.f[1 + D][iw[q]] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+      if (ic[q] < 0) continue;
+      int lw, c;
+      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      int si = sidx<P>(lw, c);
+      put_upd(S, 0, ic[q], bp[q], sm[si], ss, &bad);
+      put_upd(S, 4, ic[q], bT[q], sm[FS + si], ss, &bad);
+      if (c < n - 1 || cyc) put_upd(S, 1 + D, iu[q], bu[q], sm[2 * FS + si], ss, &bad);
+      else S.uk.f[1 + D][iu[q]] = bu[q];  // wall face: the state is kept
+      if (iw[q] >= 0) S.uk.f[1 + D][iw[q]] = bw[q];
     }
   }
   flush_norms(S, ss, bad);
@@ -456,9 +518,10 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
   float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   Group G = group_of(S, KIND, blockIdx.x, NW);
-  for (int e = threadIdx.x; e < n * NW; e += NT) {
+#pragma unroll
+  for (int q = 0; q < P; q++) {
     int lw, c;
-    elem<D, P>(e, lw, c);
+    elem<D, P>(threadIdx.x + q * NT, lw, c);
     if (lw < G.nvalid) stage_scalar<D, KIND>(S, sm, sidx<P>(lw, c), G.a, G.bb + lw, c);
   }
   __syncthreads();
@@ -525,13 +588,41 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
     for (int t = 0; t < P; t++) sm[sidx<P>(w, lane * P + t)] = xo[t];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < n * NW; e += NT) {
-    int lw, c;
-    elem<D, P>(e, lw, c);
-    if (lw >= G.nvalid) continue;
-    int i, j, k;
-    line_pos(D, G.a, G.bb + lw, c, i, j, k);
-    scalar_put(S, cc, i, j, k, sm[sidx<P>(lw, c)], ss, &bad);
+  if (!S.update) {
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+      int lw, c;
+      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      if (lw >= G.nvalid) continue;
+      int i, j, k;
+      line_pos(D, G.a, G.bb + lw, c, i, j, k);
+      scalar_put(S, cc, i, j, k, sm[sidx<P>(lw, c)], ss, &bad);
+    }
+  } else {
+    // every FP64 state value first, then the stores (see the block-line kernel)
+    int iv[P];
+    double bv[P];
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+      int lw, c;
+      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      iv[q] = -1;
+      if (lw >= G.nvalid) continue;
+      int i, j, k;
+      line_pos(D, G.a, G.bb + lw, c, i, j, k);
+      iv[q] = face_idx(g, cc, i, j, k);
+      bv[q] = S.base.f[1 + cc][iv[q]];
+    }
+#pragma unroll
+    for (int q = 0; q < P; q++) {
+      if (iv[q] < 0) continue;
+      int lw, c;
+      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      put_upd(S, 1 + cc, iv[q], bv[q], sm[sidx<P>(lw, c)], ss, &bad);
+      int i, j, k;
+      line_pos(D, G.a, G.bb + lw, c, i, j, k);
+      scalar_walls(S, cc, i, j, k);
+    }
   }
   flush_norms(S, ss, bad);
 }
