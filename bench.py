@@ -52,6 +52,26 @@ HBM_PEAK_GBS = 6780.4     # measured copy bandwidth of the GB300s
 #   avg           : U^n and U^k in (2 x 5 x 8) + Ubar out (5 x 4)                      = 100
 MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rhs": 100, "coef": 76, "avg": 100}
 
+# DRAM traffic of each mixed stage measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over the stage's launches in one Picard iteration, per
+# grid point; profiles/stages_bubble_128x256x256_mixed.md) and the hash of the
+# kernel sources it was measured on: reported only while the sources match.
+MEASURED_TRAFFIC = {}
+TRAFFIC_SOURCE_HASH = None
+
+
+def kernel_source_hash():
+    """sha256 (first 16 hex digits) of the CUDA sources and the C header"""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(root, "paper_2004_13887_gb300", "csrc")
+    h = hashlib.sha256()
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    for f in files + [os.path.join(root, "include", "sph.h")]:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
@@ -135,6 +155,24 @@ def oracle_sample(steps: int):
 
 # ------------------------------------------------------------- our arm
 
+def max_over_ranks(ms, dist, device="cuda"):
+    """The job's time is the slowest replica's: an all-reduce MAX of each rank's
+    CUDA-event time (the only collective of the benchmark; replicas exchange no
+    data)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank, steps, world, t_max_ms):
+    """grid-point updates/s of the whole job: every rank advances its own copy
+    of the workload (weak scaling), timed by the slowest rank"""
+    return points_per_rank * steps * world / (t_max_ms / 1e3)
+
+
 def time_path(solver, args, dist, local):
     """warm-up, then the timed steps (CUDA events on the library's stream)"""
     import torch
@@ -161,12 +199,7 @@ def time_path(solver, args, dist, local):
     clocks = sampler.stop()
     if dist is not None:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(e0.elapsed_time(e1), dist)
     return t_max, kern, launches, clocks
 
 
@@ -218,7 +251,7 @@ def run_ours(args, rank, world, dist):
         del s64
         torch.cuda.empty_cache()
     if args.only == "fp64":
-        return {"metric": METRIC, "value": N * args.steps * world / (t64 / 1e3), "unit": UNIT, "n_gpus": world,
+        return {"metric": METRIC, "value": job_throughput(N, args.steps, world, t64), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64 / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64"}}
@@ -229,12 +262,12 @@ def run_ours(args, rank, world, dist):
     stream = solver.stream
 
     t_max, kern, launches, clocks = time_path(solver, args, dist, local)
-    value = N * args.steps * world / (t_max / 1e3)
+    value = job_throughput(N, args.steps, world, t_max)
     Um = [f.cpu().numpy() for f in solver.get_state()]
     errors, fp64 = None, None
     if U64 is not None:
         errors = {"metric": "relative L2 after warmup+steps steps", **field_errors(Um, U64, c)}
-        fp64 = {"value": N * args.steps * world / (t64 / 1e3), "ms_per_step": t64 / args.steps,
+        fp64 = {"value": job_throughput(N, args.steps, world, t64), "ms_per_step": t64 / args.steps,
                 "kernel_shares": {k: round(v[0] / max(sum(x[0] for x in kern64.values()), 1e-30), 4)
                                   for k, v in kern64.items() if v[1]}}
 
@@ -243,9 +276,12 @@ def run_ours(args, rank, world, dist):
     dom_ms, dom_n = kern[dom]
     per_launch_ms = dom_ms / max(dom_n, 1)
     bpp = MIXED_BYTES_PER_POINT.get(dom)
+    traffic = None
+    if dom in MEASURED_TRAFFIC and TRAFFIC_SOURCE_HASH == kernel_source_hash():
+        traffic = MEASURED_TRAFFIC[dom] * N   # bytes per stage launch
     roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "peak": HBM_PEAK_GBS,
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "launch_ms": per_launch_ms, "traffic": None, "bytes_per_point": bpp}
+            "launch_ms": per_launch_ms, "traffic": traffic, "bytes_per_point": bpp}
     if bpp:
         achieved = bpp * N / (per_launch_ms * 1e-3) / 1e9
         roof.update(achieved=achieved, frac=achieved / HBM_PEAK_GBS)
@@ -270,7 +306,7 @@ def run_ours(args, rank, world, dist):
         out = solver.get_state(device=False)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = N * e2e_steps * world / e2e_s
+    e2e_value = job_throughput(N, e2e_steps, world, e2e_s * 1e3)
     solver.close()
 
     line = {
