@@ -56,8 +56,8 @@ MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rh
 # dram__bytes_write.sum over the stage's launches in one Picard iteration, per
 # grid point; profiles/stages_bubble_128x256x256_mixed.md) and the hash of the
 # kernel sources it was measured on: reported only while the sources match.
-MEASURED_TRAFFIC = {}
-TRAFFIC_SOURCE_HASH = None
+MEASURED_TRAFFIC = {"avg": 86.4, "coef": 69.2, "rhs": 160.8, "sweep_r": 87.0, "sweep_theta": 90.5, "sweep_phi": 152.5}
+TRAFFIC_SOURCE_HASH = "679c2a1165011485"
 
 
 def kernel_source_hash():
