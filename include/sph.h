@@ -94,6 +94,37 @@ int sph_get_state(sph_ctx* ctx, double* const* fields, int on_device);
 int sph_step(sph_ctx* ctx, double dt, int n_iter, const double* const* source, int source_on_device,
              double* residual_out);
 
+/* sph_step without waiting: the step is only enqueued on the context's
+ * stream (so it can be captured into a CUDA graph).  source: NULL or 5 device
+ * arrays (host sources are SPH_ERR_ARG).  The non-finite / zero-pivot flags of
+ * enqueued steps accumulate until sph_status, which synchronises the stream,
+ * returns SPH_ERR_NONFINITE or SPH_ERR_SINGULAR if any step since the last
+ * sph_status raised one (the state is then not usable; U^n is not restored),
+ * clears the flags and optionally writes the residual of the last step.
+ * sph_step itself clears pending flags. */
+int sph_step_async(sph_ctx* ctx, double dt, int n_iter, const double* const* source, int source_on_device);
+int sph_status(sph_ctx* ctx, double* residual_out);
+
+/* Batches of independent contexts (an ensemble of problems, e.g. of different
+ * grid sizes) stepped by one CUDA graph.  sph_batch_create: n distinct contexts
+ * of one device with non-NULL streams (ideally one stream each), and the
+ * non-NULL stream `stream` the graph runs on.  sph_batch_capture: records `steps` (even, >= 2)
+ * sph_step_async calls of every context into a graph whose branches -- one per
+ * context, on the context's stream -- run concurrently (per-kernel timing must
+ * be off; contexts sharing a stream run one after the other in the graph).
+ * sph_batch_launch: replays it `times` times on `stream` (each replay
+ * advances every context by `steps` steps); SPH_ERR_ARG if a context was
+ * stepped an odd number of times since the capture (its state moved to the
+ * other buffer).  sph_batch_status: synchronises and returns the first
+ * context's error (index in *first_bad, -1 if none), clearing all flags.
+ * The contexts stay usable individually; destroy the batch before them. */
+typedef struct sph_batch sph_batch;
+int sph_batch_create(sph_ctx* const* ctxs, int n, void* stream, sph_batch** out);
+int sph_batch_capture(sph_batch* batch, double dt, int n_iter, int steps);
+int sph_batch_launch(sph_batch* batch, int times);
+int sph_batch_status(sph_batch* batch, int* first_bad);
+void sph_batch_destroy(sph_batch* batch);
+
 /* Stage entry points (the same kernels sph_step runs), for testing each part.
  * sph_set_iterate: copy 5 fields into the iterate U^{n+1,k} (default: U^n).
  * sph_rhs: R = -(U^k - U^n) - dt [N(Ubar) + G - S], Ubar = (U^k + U^n)/2, the

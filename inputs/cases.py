@@ -238,6 +238,24 @@ def bubble(n=(128, 256, 256), seed: int = 1, dt: float = 1.0, steps: int = 200, 
                 info=dict(seed=seed, radius=radius, altitude=altitude, amplitude=amplitude))
 
 
+ENSEMBLE_SEED = 20041389
+
+
+def ensemble_specs(count: int = 64, seed: int = ENSEMBLE_SEED):
+    """The batched ensemble: `count` independent bubbles on uneven grids of the
+    same sector, nr uniform in {16, 32, 48, 64}, n_theta and n_phi uniform in
+    {64, 128, 192, 256}, amplitude uniform in [0.2, 1] K, radius uniform in
+    [1, 3] km; the per-instance seed drives the bubble's jitter."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        n = (int(rng.choice([16, 32, 48, 64])), int(rng.choice([64, 128, 192, 256])),
+             int(rng.choice([64, 128, 192, 256])))
+        out.append(dict(n=n, seed=int(rng.integers(1, 2 ** 31 - 1)), amplitude=float(rng.uniform(0.2, 1.0)),
+                        radius=float(rng.uniform(1000.0, 3000.0))))
+    return out
+
+
 def rest_state(grid: Grid, hydrostatic: bool = True) -> Case:
     """Air at rest over the discretely balanced background (no perturbation)."""
     par = Params(gamma=AIR["cp"] / AIR["cv"], cv=AIR["cv"], Pr=AIR["Pr"], mu=AIR["mu"],

@@ -16,7 +16,7 @@ import numpy as np
 
 from ._build import LIB, build
 
-__all__ = ["build", "load", "Solver", "SphError", "sph_field_size", "SPH_PREC_FP64", "SPH_PREC_MIXED",
+__all__ = ["build", "load", "Solver", "Batch", "SphError", "sph_field_size", "SPH_PREC_FP64", "SPH_PREC_MIXED",
            "SPH_LINES_THOMAS", "SPH_LINES_PARTITIONED"]
 
 SPH_PREC_FP64 = 0
@@ -58,6 +58,13 @@ SIGNATURES = {
     "sph_set_state": ([_CTX, _PP, C.c_int], C.c_int),
     "sph_get_state": ([_CTX, _PP, C.c_int], C.c_int),
     "sph_step": ([_CTX, C.c_double, C.c_int, _PP, C.c_int, _DP], C.c_int),
+    "sph_step_async": ([_CTX, C.c_double, C.c_int, _PP, C.c_int], C.c_int),
+    "sph_status": ([_CTX, _DP], C.c_int),
+    "sph_batch_create": ([C.POINTER(_CTX), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "sph_batch_capture": ([C.c_void_p, C.c_double, C.c_int, C.c_int], C.c_int),
+    "sph_batch_launch": ([C.c_void_p, C.c_int], C.c_int),
+    "sph_batch_status": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
+    "sph_batch_destroy": ([C.c_void_p], None),
     "sph_set_iterate": ([_CTX, _PP, C.c_int], C.c_int),
     "sph_rhs": ([_CTX, C.c_double, _PP, C.c_int, _PP], C.c_int),
     "sph_sweep": ([_CTX, C.c_int, C.c_double, _PP, _PP], C.c_int),
@@ -222,6 +229,17 @@ class Solver:
                                res.ctypes.data_as(_DP) if res is not None else None), "sph_step")
         return res
 
+    def step_async(self, dt: float, n_iter: int, source=None):
+        """Enqueue one step on the solver's stream (device sources only); check with status()."""
+        src = _Ptrs(source, self.shapes, True) if source is not None else None
+        _check(load().sph_step_async(self._h, float(dt), int(n_iter), src.arr if src else None, 1), "sph_step_async")
+
+    def status(self, residual: bool = False):
+        """Synchronise; raise if an enqueued step produced a non-finite value or a zero pivot."""
+        res = np.zeros(5) if residual else None
+        _check(load().sph_status(self._h, res.ctypes.data_as(_DP) if res is not None else None), "sph_status")
+        return res
+
     # ------------------------------------------------------------- stages
     def rhs(self, dt: float, source=None):
         out = self.empty()
@@ -265,6 +283,48 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             load().sph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent solvers stepped together by one CUDA graph (sph_batch_*):
+    each solver's steps form a branch on its own stream, so the instances run
+    concurrently and no host launch overhead remains per step."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        arr = (_CTX * len(self.solvers))(*[s._h for s in self.solvers])
+        h = C.c_void_p()
+        _check(load().sph_batch_create(arr, len(self.solvers), C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+               "sph_batch_create")
+        self._h = h
+        self.steps = 0
+
+    def capture(self, dt: float, n_iter: int, steps: int = 2):
+        _check(load().sph_batch_capture(self._h, float(dt), int(n_iter), int(steps)), "sph_batch_capture")
+        self.steps = steps
+
+    def launch(self, times: int = 1):
+        _check(load().sph_batch_launch(self._h, int(times)), "sph_batch_launch")
+
+    def status(self):
+        """Synchronise; raise SphError for the first failed solver (its index in .bad)."""
+        bad = C.c_int(-1)
+        code = load().sph_batch_status(self._h, C.byref(bad))
+        self.bad = bad.value
+        _check(code, f"sph_batch_status (solver {bad.value})")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sph_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

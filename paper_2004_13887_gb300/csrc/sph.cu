@@ -1023,6 +1023,8 @@ static int upload_background(sph_ctx* c, const double* pref, const double* Tref)
   return e;
 }
 
+static int lines_prepare(const sph_ctx* c);
+
 extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream, sph_ctx** out) {
   if (!gr || !pa || !out) return SPH_ERR_ARG;
   *out = NULL;
@@ -1106,6 +1108,7 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   err = (zb && tb) ? upload_background(c, zb, tb) : SPH_ERR_NOMEM;
   free(zb); free(tb);
   if (err != SPH_OK) { free_all(c); free(c); return err; }
+  if (mixed && (err = lines_prepare(c)) != SPH_OK) { free_all(c); free(c); return err; }
   c->cur = 0;
   *out = c;
   return SPH_OK;
@@ -1305,11 +1308,17 @@ static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
 
 // Partitioned line solver (mixed path) for lines of n = 32 P cells: one
 // launch per line kind, one block per group of 32/P lines.
-template <typename K>
-static int lines_smem(K kern, size_t smem) {
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+// The shared-memory size attribute of the three kernels of a (D, P), set once
+// per process (at context creation, so that no attribute call falls inside a
+// CUDA graph capture).
+template <int D, int P>
+static int lines_attr() {
+  static int done = 0;
+  if (done) return SPH_OK;
+  const int smb = lines::NFB * lines::FS * (int)sizeof(float);
+  if (cudaFuncSetAttribute(lines::k_lines_blk<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) != cudaSuccess)
     return SPH_ERR_CUDA;
+  done = 1;
   return SPH_OK;
 }
 
@@ -1333,25 +1342,36 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
   const size_t sms = (size_t)lines::NFS * lines::FS * sizeof(float);
   int ng, e;
   k_begin(c, SPH_K_SWEEP_R + D);
+  if ((e = lines_attr<D, P>())) return e;
   if ((ng = lines_groups(S, 0, NW)) > 0) {
     // one factor slot per block
     if ((size_t)ng * NW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
-    if ((e = lines_smem(lines::k_lines_blk<D, P>, smb))) return e;
     lines::k_lines_blk<D, P><<<ng, NT, smb, c->st>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 1, NW)) > 0) {
-    if ((e = lines_smem(lines::k_lines_sca<D, P, 1>, sms))) return e;
     lines::k_lines_sca<D, P, 1><<<ng, NT, sms, c->st>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 2, NW)) > 0) {
-    if ((e = lines_smem(lines::k_lines_sca<D, P, 2>, sms))) return e;
     lines::k_lines_sca<D, P, 2><<<ng, NT, sms, c->st>>>(S);
     c->launches++;
   }
   c->launches--;  // launch_ok counts one more
   return launch_ok(c);
+}
+
+template <int D>
+static int lines_attr_d(int n) {
+  return n == 64 ? lines_attr<D, 2>() : n == 128 ? lines_attr<D, 4>() : n == 256 ? lines_attr<D, 8>() : SPH_OK;
+}
+
+static int lines_prepare(const sph_ctx* c) {
+  const Geo<double>& g = c->d64.g;
+  int e = lines_attr_d<0>(g.nr);
+  if (!e) e = lines_attr_d<1>(g.nt);
+  if (!e) e = lines_attr_d<2>(g.np);
+  return e;
 }
 
 template <int D>
@@ -1495,6 +1515,39 @@ static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> s
   return e;
 }
 
+// Enqueue one step without waiting for it (no status read): the flags of
+// enqueued steps accumulate until sph_status.  Only device sources (or none),
+// so that nothing is copied from host memory.
+extern "C" int sph_step_async(sph_ctx* c, double dt, int n_iter, const double* const* source, int on_device) {
+  if (!c || !(dt > 0) || n_iter < 1 || (source && !on_device)) return SPH_ERR_ARG;
+  CF<double> src;
+  int has = stage_source(c, source, on_device, &src);
+  if (has < 0) return SPH_ERR_CUDA;
+  int e = c->prec == SPH_PREC_MIXED ? step_impl(c, c->d32, dt, n_iter, src, has)
+                                    : step_impl(c, c->d64, dt, n_iter, src, has);
+  if (e) return e;
+  c->cur = 1 - c->cur;
+  c->iterate_set = 0;
+  return SPH_OK;
+}
+
+extern "C" int sph_status(sph_ctx* c, double* residual_out) {
+  if (!c) return SPH_ERR_ARG;
+  int flag = 0, e;
+  if ((e = read_flag(c, &flag))) return e;
+  if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->st) != cudaSuccess) return SPH_ERR_CUDA;
+  if (residual_out) {
+    double s[5];
+    if (cudaMemcpyAsync(s, c->acc, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+      return SPH_ERR_CUDA;
+    for (int f = 0; f < 5; f++) residual_out[f] = c->unknowns[f] > 0 ? sqrt(s[f] / (double)c->unknowns[f]) : 0.0;
+  }
+  if (flag & FLAG_SINGULAR) return SPH_ERR_SINGULAR;
+  if (flag & FLAG_NONFINITE) return SPH_ERR_NONFINITE;
+  return SPH_OK;
+}
+
 extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* source, int on_device,
                         double* residual_out) {
   if (!c || !(dt > 0) || n_iter < 1) return SPH_ERR_ARG;
@@ -1517,4 +1570,123 @@ extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* 
   c->cur = 1 - c->cur;
   c->iterate_set = 0;
   return SPH_OK;
+}
+
+// ------------------------------------------------------------ batches
+
+struct sph_batch {
+  int n;
+  sph_ctx** c;
+  cudaStream_t st;
+  cudaEvent_t fork;
+  cudaEvent_t* join;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int* cur;                // each context's U^n buffer at capture
+  long long* nlaunch;      // kernels one replay launches per context
+};
+
+extern "C" void sph_batch_destroy(sph_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (int q = 0; q < b->n && b->join; q++)
+    if (b->join[q]) cudaEventDestroy(b->join[q]);
+  free(b->join);
+  free(b->c);
+  free(b->cur);
+  free(b->nlaunch);
+  free(b);
+}
+
+extern "C" int sph_batch_create(sph_ctx* const* ctxs, int n, void* stream, sph_batch** out) {
+  if (!ctxs || n < 1 || !stream || !out) return SPH_ERR_ARG;
+  *out = NULL;
+  for (int q = 0; q < n; q++) {
+    if (!ctxs[q] || !ctxs[q]->st) return SPH_ERR_ARG;
+    for (int r = 0; r < q; r++)
+      if (ctxs[r] == ctxs[q]) return SPH_ERR_ARG;
+  }
+  sph_batch* b = (sph_batch*)calloc(1, sizeof(sph_batch));
+  if (!b) return SPH_ERR_NOMEM;
+  b->n = n;
+  b->st = (cudaStream_t)stream;
+  b->c = (sph_ctx**)calloc(n, sizeof(sph_ctx*));
+  b->join = (cudaEvent_t*)calloc(n, sizeof(cudaEvent_t));
+  b->cur = (int*)calloc(n, sizeof(int));
+  b->nlaunch = (long long*)calloc(n, sizeof(long long));
+  if (!b->c || !b->join || !b->cur || !b->nlaunch) { sph_batch_destroy(b); return SPH_ERR_NOMEM; }
+  int err = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+  for (int q = 0; q < n && !err; q++) {
+    b->c[q] = ctxs[q];
+    if (cudaEventCreateWithFlags(&b->join[q], cudaEventDisableTiming) != cudaSuccess) err = SPH_ERR_CUDA;
+  }
+  if (err) { sph_batch_destroy(b); return err; }
+  *out = b;
+  return SPH_OK;
+}
+
+extern "C" int sph_batch_capture(sph_batch* b, double dt, int n_iter, int steps) {
+  if (!b || !(dt > 0) || n_iter < 1 || steps < 2 || (steps & 1)) return SPH_ERR_ARG;
+  for (int q = 0; q < b->n; q++)
+    if (b->c[q]->prof) return SPH_ERR_ARG;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = NULL; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = NULL; }
+  for (int q = 0; q < b->n; q++) { b->cur[q] = b->c[q]->cur; b->nlaunch[q] = b->c[q]->launches; }
+  if (cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SPH_ERR_CUDA;
+  int err = cudaEventRecord(b->fork, b->st) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+  for (int q = 0; q < b->n && !err; q++)
+    if (cudaStreamWaitEvent(b->c[q]->st, b->fork, 0) != cudaSuccess) err = SPH_ERR_CUDA;
+  // steps is even: every context's U^n ends in the buffer it started in, so
+  // the graph can be replayed
+  for (int s = 0; s < steps && !err; s++)
+    for (int q = 0; q < b->n && !err; q++) err = sph_step_async(b->c[q], dt, n_iter, NULL, 0);
+  for (int q = 0; q < b->n && !err; q++)
+    if (cudaEventRecord(b->join[q], b->c[q]->st) != cudaSuccess || cudaStreamWaitEvent(b->st, b->join[q], 0) != cudaSuccess)
+      err = SPH_ERR_CUDA;
+  cudaGraph_t g = NULL;
+  cudaError_t ce = cudaStreamEndCapture(b->st, &g);
+  if (!err && ce != cudaSuccess) err = SPH_ERR_CUDA;
+  if (!err && cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) err = SPH_ERR_CUDA;
+  for (int q = 0; q < b->n; q++) {
+    // capturing launched nothing: count a replay's launches on each launch
+    b->nlaunch[q] = b->c[q]->launches - b->nlaunch[q];
+    b->c[q]->launches -= b->nlaunch[q];
+  }
+  if (err) {
+    if (g) cudaGraphDestroy(g);
+    b->exec = NULL;
+    cudaGetLastError();
+    return err;
+  }
+  b->graph = g;
+  return SPH_OK;
+}
+
+extern "C" int sph_batch_launch(sph_batch* b, int times) {
+  if (!b || !b->exec || times < 0) return SPH_ERR_ARG;
+  // the graph holds the buffers of the capture: a context stepped an odd number
+  // of times since then has its U^n in the other buffer
+  for (int q = 0; q < b->n; q++)
+    if (b->c[q]->cur != b->cur[q]) return SPH_ERR_ARG;
+  for (int t = 0; t < times; t++)
+    if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return SPH_ERR_CUDA;
+  for (int q = 0; q < b->n; q++) b->c[q]->launches += b->nlaunch[q] * times;
+  return SPH_OK;
+}
+
+extern "C" int sph_batch_status(sph_batch* b, int* first_bad) {
+  if (!b) return SPH_ERR_ARG;
+  if (first_bad) *first_bad = -1;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return SPH_ERR_CUDA;
+  int worst = SPH_OK;
+  for (int q = 0; q < b->n; q++) {
+    int e = sph_status(b->c[q], NULL);
+    if (e != SPH_OK && worst == SPH_OK) {
+      worst = e;
+      if (first_bad) *first_bad = q;
+    }
+  }
+  return worst;
 }

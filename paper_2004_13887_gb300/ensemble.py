@@ -1,0 +1,96 @@
+"""Batched ensembles of independent problems of different sizes: one solver
+per instance (mixed precision), stepped together by a CUDA graph (Batch),
+with the line solver of each grid shape chosen by timing (autotune)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import SPH_LINES_PARTITIONED, SPH_LINES_THOMAS, SPH_PREC_MIXED, Batch, Solver
+
+
+def _partitioned_applies(grid) -> bool:
+    return any(n in (64, 128, 256) for n in (grid.nr, grid.nt, grid.np))
+
+
+def time_steps(solver, dt, n_iter, steps=2, warmup=1):
+    """milliseconds per step on the solver's stream (CUDA events)"""
+    import torch
+    for _ in range(warmup):
+        solver.step_async(dt, n_iter)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(solver.stream)
+    for _ in range(steps):
+        solver.step_async(dt, n_iter)
+    e1.record(solver.stream)
+    solver.status()
+    return e0.elapsed_time(e1) / steps
+
+
+def autotune(cases, dt, n_iter):
+    """For every distinct grid shape among the cases, the faster line solver of
+    the mixed mode (partitioned or block Thomas), timed on a scratch solver
+    started from that shape's first case.  Returns {shape: SPH_LINES_*}."""
+    import torch
+    choice = {}
+    for c in cases:
+        shape = (c.grid.nr, c.grid.nt, c.grid.np)
+        if shape in choice:
+            continue
+        if not _partitioned_applies(c.grid):
+            choice[shape] = SPH_LINES_THOMAS
+            continue
+        best, best_ms = None, None
+        for which in (SPH_LINES_PARTITIONED, SPH_LINES_THOMAS):
+            s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
+            s.set_background(*c.bg)
+            s.set_state([torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in c.init])
+            s.set_line_solver(which)
+            ms = time_steps(s, dt, n_iter)
+            s.close()
+            if best_ms is None or ms < best_ms:
+                best, best_ms = which, ms
+        choice[shape] = best
+    return choice
+
+
+class Ensemble:
+    """cases: objects with grid, par, bg, init (inputs.cases.Case).  Each gets
+    a mixed-precision solver on its own stream; step() replays a graph of
+    `graph_steps` steps of all of them."""
+
+    def __init__(self, cases, dt, n_iter=2, tune=True, graph_steps=2):
+        import torch
+        self.cases = list(cases)
+        self.dt, self.n_iter = dt, n_iter
+        self.choice = autotune(self.cases, dt, n_iter) if tune else {}
+        self.solvers = []
+        for c in self.cases:
+            s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
+            s.set_background(*c.bg)
+            s.set_state([torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in c.init])
+            shape = (c.grid.nr, c.grid.nt, c.grid.np)
+            if shape in self.choice:
+                s.set_line_solver(self.choice[shape])
+            self.solvers.append(s)
+        torch.cuda.synchronize()
+        self.batch = Batch(self.solvers)
+        self.batch.capture(dt, n_iter, graph_steps)
+        self.graph_steps = graph_steps
+
+    @property
+    def points(self) -> int:
+        return sum(c.grid.nr * c.grid.nt * c.grid.np for c in self.cases)
+
+    def run(self, steps):
+        """advance every instance by `steps` (a multiple of graph_steps) steps"""
+        if steps % self.graph_steps:
+            raise ValueError(f"steps must be a multiple of {self.graph_steps}")
+        self.batch.launch(steps // self.graph_steps)
+
+    def status(self):
+        self.batch.status()
+
+    def close(self):
+        self.batch.close()
+        for s in self.solvers:
+            s.close()

@@ -1,0 +1,146 @@
+"""Batched ensembles (independent problems of different sizes stepped by one
+CUDA graph whose branches run concurrently), the enqueue-only step and its
+status, and the per-shape line-solver autotuner."""
+import numpy as np
+import pytest
+
+import paper_2004_13887_gb300 as sph
+from paper_2004_13887_gb300 import ensemble
+from inputs import cases
+from tests.gpu_helpers import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+MIXED = sph.SPH_PREC_MIXED
+
+# uneven grids: partitioned lengths (64, 128) next to block Thomas ones (16, 48, 192)
+SHAPES = [(16, 64, 64), (32, 64, 128), (16, 128, 64), (48, 64, 64), (32, 192, 64), (64, 64, 128)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    sph.build()
+
+
+def _cases():
+    return [cases.bubble(n, seed=10 + q, dt=1.0, amplitude=0.2 + 0.1 * q, radius=1500.0 + 200.0 * q)
+            for q, n in enumerate(SHAPES)]
+
+
+def _solver(c, prec=MIXED):
+    import torch
+    s = sph.Solver(c.grid, c.par, precision=prec, stream=torch.cuda.Stream())
+    s.set_background(*c.bg)
+    s.set_state(to_dev(c.init))
+    return s
+
+
+def test_batch_graph_equals_individual_steps():
+    """Replaying the captured graph gives bit-for-bit the states of stepping
+    each solver on its own (same kernels, same inputs)."""
+    cs = _cases()
+    ref = []
+    for c in cs:
+        s = _solver(c)
+        for _ in range(4):
+            s.step(c.dt, 2)
+        ref.append(to_host(s.get_state()))
+        s.close()
+    solvers = [_solver(c) for c in cs]
+    b = sph.Batch(solvers)
+    b.capture(1.0, 2, steps=2)
+    b.launch(2)
+    b.status()
+    for q, s in enumerate(solvers):
+        got = to_host(s.get_state())
+        for f in range(5):
+            assert np.array_equal(got[f], ref[q][f]), (SHAPES[q], f)
+    b.close()
+
+
+def test_step_async_equals_step():
+    c = _cases()[1]
+    a, b = _solver(c), _solver(c)
+    for _ in range(3):
+        a.step(c.dt, 2)
+        b.step_async(c.dt, 2)
+    res = b.status(residual=True)
+    assert res is not None and np.all(np.isfinite(res))
+    for f in range(5):
+        assert np.array_equal(to_host(a.get_state())[f], to_host(b.get_state())[f])
+
+
+def test_batch_status_reports_the_failed_instance():
+    cs = _cases()[:3]
+    bad = [f.copy() for f in cs[2].init]
+    bad[4][1, 2, 3] = np.nan
+    solvers = [_solver(c) for c in cs]
+    solvers[2].set_state(to_dev(bad))
+    b = sph.Batch(solvers)
+    b.capture(1.0, 2, steps=2)
+    b.launch(1)
+    with pytest.raises(sph.SphError):
+        b.status()
+    assert b.bad == 2
+    b.close()
+
+
+def test_batch_refuses_a_state_in_the_other_buffer():
+    cs = _cases()[:2]
+    solvers = [_solver(c) for c in cs]
+    b = sph.Batch(solvers)
+    b.capture(1.0, 2, steps=2)
+    solvers[0].step(1.0, 2)       # one step outside the graph: U^n moved buffers
+    with pytest.raises(sph.SphError):
+        b.launch(1)
+    solvers[0].step(1.0, 2)       # back in the captured buffer
+    b.launch(1)
+    b.status()
+    with pytest.raises(sph.SphError):
+        b.capture(1.0, 2, steps=3)   # odd step counts cannot be replayed
+    b.close()
+
+
+def test_autotune_choices_agree():
+    cs = _cases()
+    choice = ensemble.autotune(cs, 1.0, 2)
+    assert set(choice) == {(c.grid.nr, c.grid.nt, c.grid.np) for c in cs}
+    assert all(v in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED) for v in choice.values())
+    c = cs[5]   # 64 x 64 x 128: both solvers apply
+    xs = []
+    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED):
+        s = _solver(c)
+        s.set_line_solver(which)
+        for _ in range(2):
+            s.step(c.dt, 2)
+        xs.append(to_host(s.get_state()))
+        s.close()
+    for f in range(5):
+        scale = float(np.max(np.abs(xs[0][f] - c.init[f]))) or 1.0
+        assert float(np.max(np.abs(xs[0][f] - xs[1][f]))) <= 1e-5 * scale
+
+
+def test_ensemble_of_config_five():
+    """The 64-instance ensemble (uneven grids, random bubbles): 10 steps through
+    the graph, every instance finite, and two instances against the FP64 mode
+    (relative L2 of T and u <= 1e-6)."""
+    specs = cases.ensemble_specs()
+    cs = [cases.bubble(sp["n"], seed=sp["seed"], dt=1.0, amplitude=sp["amplitude"], radius=sp["radius"])
+          for sp in specs]
+    ens = ensemble.Ensemble(cs, dt=1.0, n_iter=2)
+    ens.run(10)
+    ens.status()
+    for q in (0, 37):
+        c = cs[q]
+        got = to_host(ens.solvers[q].get_state())
+        assert all(np.all(np.isfinite(f)) for f in got)
+        s = _solver(c, prec=sph.SPH_PREC_FP64)
+        for _ in range(10):
+            s.step(c.dt, 2)
+        ref = to_host(s.get_state())
+        s.close()
+        T = lambda U: U[4] + c.bg[1][1:-1][:, None, None]
+        assert np.linalg.norm(T(got) - T(ref)) <= 1e-6 * np.linalg.norm(T(ref))
+        du = sum(np.linalg.norm(got[k] - ref[k]) ** 2 for k in (1, 2, 3)) ** 0.5
+        nu = sum(np.linalg.norm(ref[k]) ** 2 for k in (1, 2, 3)) ** 0.5
+        assert du <= 1e-6 * nu, (q, du, nu)
+    ens.close()
