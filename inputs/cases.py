@@ -256,6 +256,54 @@ def ensemble_specs(count: int = 64, seed: int = ENSEMBLE_SEED):
     return out
 
 
+# ------------------------------------------------------------------ full sphere
+
+SHELL_SEED = 20041390
+
+
+def full_sphere_grid(n=(64, 512, 1024), r1: float = 6371e3, r2: float = 6381e3) -> Grid:
+    """The whole sphere: theta in [0, pi] (pole faces), phi periodic."""
+    return Grid(n[0], n[1], n[2], r1, r2, 0.0, math.pi, 0.0, 2 * math.pi, periodic=True)
+
+
+def shell_low_mach(n=(64, 512, 1024), M0: float = 1e-4, seed: int = SHELL_SEED, dt: float = 1.0,
+                   steps: int = 50, K: int = 2, grid: Grid = None) -> Case:
+    """Full spherical shell of air at rest (p0 = 1e5 Pa, T0 = 300 K, no
+    gravity) with a smooth random velocity of Mach number M0: amplitude
+    M0 c0 times a sum of low spherical modes with seeded coefficients, plus
+    1e-3 of that amplitude in smooth seeded noise.  u_r vanishes on the radial
+    walls, u_theta and u_phi carry sin(theta), so the field is compatible with
+    the walls and the poles; the thermodynamic state starts uniform."""
+    grid = full_sphere_grid(n) if grid is None else grid
+    rng = np.random.default_rng(seed)
+    par = Params(gamma=AIR["cp"] / AIR["cv"], cv=AIR["cv"], Pr=AIR["Pr"], mu=AIR["mu"], g=0.0)
+    p0, T0 = 1.0e5, 300.0
+    c0 = math.sqrt(par.gamma * p0 / (p0 / (par.cv * (par.gamma - 1.0) * T0)))
+    amp = M0 * c0
+    coef = rng.standard_normal((3, 4, 4, 2))
+    noise = rng.standard_normal((3, 8, 8, 2)) * 1e-3 / 8.0
+    def field(c, R, TH, PH):
+        xi = (R - grid.r1) / (grid.r2 - grid.r1)
+        v = 0.0
+        for m in range(4):
+            for l in range(4):
+                v = v + np.cos(TH) ** l * (coef[c, m, l, 0] * np.cos(m * PH) + coef[c, m, l, 1] * np.sin(m * PH))
+        for m in range(8):
+            for l in range(8):
+                v = v + np.cos(TH) ** l * (noise[c, m, l, 0] * np.cos(m * PH) + noise[c, m, l, 1] * np.sin(m * PH))
+        return amp * v * (np.sin(math.pi * xi) if c == 0 else np.sin(TH))
+    U = grid.zeros()
+    for c in range(3):
+        R, TH, PH = grid.coords(1 + c)
+        U[1 + c] = np.array(np.broadcast_to(field(c, R, TH, PH), grid.shapes()[1 + c]))
+    U[1][0] = U[1][-1] = 0.0          # radial walls
+    U[2][:, 0] = U[2][:, -1] = 0.0    # pole faces
+    for c in (1, 2, 3):               # peak speed of each component = M0 c0
+        U[c] *= amp / max(float(np.max(np.abs(U[c]))), 1e-300)
+    bg = _const_bg(grid, p0, T0)
+    return Case("shell_low_mach", grid, par, dt, steps, K, bg, U, info=dict(M0=M0, c0=c0, p0=p0, T0=T0))
+
+
 def rest_state(grid: Grid, hydrostatic: bool = True) -> Case:
     """Air at rest over the discretely balanced background (no perturbation)."""
     par = Params(gamma=AIR["cp"] / AIR["cv"], cv=AIR["cv"], Pr=AIR["Pr"], mu=AIR["mu"],
