@@ -107,14 +107,14 @@ __device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<
   // precision for it.
   R pref = g.pcen[i], Tref = g.Tcen[i];
   R pp = ub.f[0][t], Tp = ub.f[4][t];
-  R pb = pref + pp, tb = Tref + Tp;
+  Thermo<R> th = thermo(g, P, i, pp, Tp);
   R iRg = pick<R>(1.0 / P.Rg, P.iRg_f);
-  R itb = sdiv(R(1), tb);
-  c.Pb[t] = pb;
-  c.Tb[t] = tb;
-  c.rho[t] = pb * itb * iRg;
+  R itb = sdiv(R(1), th.Tb);
+  c.Pb[t] = th.Pb;
+  c.Tb[t] = th.Tb;
+  c.rho[t] = th.rho;
   c.drho[t] = sdiv((pp * Tref - pref * Tp) * itb * iRg, Tref);
-  c.beta[t] = sdiv((pick<R>(P.gamma, P.gamma_f) - R(1)) * tb, pb);
+  c.beta[t] = th.beta;
   R ur = hr<CIJ>(g, UR, i, j, k), ut = ht<CIJ>(g, UT, i, j, k), up = hp<CIJ>(g, UP, i, j, k);
   c.uc0[t] = ur; c.uc1[t] = ut; c.uc2[t] = up;
   R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j], h = R(0.5);
@@ -226,12 +226,12 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
   R divu;
   if constexpr (sizeof(R) == sizeof(double)) divu = div_ubar(gd, un, uk, i, j, k);
   else divu = div_ubar_ff(g, ub, ul, i, j, k);
-  R xrt = (ht<CIJ>(g, UT, i + 1, j, k) - ht<CIJ>(g, UT, i - 1, j, k)) * h * g.idr
-        + (hr<CIJ>(g, UR, i, j + 1, k) - hr<CIJ>(g, UR, i, j - 1, k)) * h * ir * g.idth;
-  R xrp = (hp<CIJ>(g, UP, i + 1, j, k) - hp<CIJ>(g, UP, i - 1, j, k)) * h * g.idr
-        + (hr<CIJ>(g, UR, i, j, k + 1) - hr<CIJ>(g, UR, i, j, k - 1)) * h * ir * is * g.idph;
-  R xtp = (hp<CIJ>(g, UP, i, j + 1, k) - hp<CIJ>(g, UP, i, j - 1, k)) * h * ir * g.idth
-        + (ht<CIJ>(g, UT, i, j, k + 1) - ht<CIJ>(g, UT, i, j, k - 1)) * h * ir * is * g.idph;
+  R xrt = (htc<CIJ>(g, c, UT, i + 1, j, k) - htc<CIJ>(g, c, UT, i - 1, j, k)) * h * g.idr
+        + (hrc<CIJ>(g, c, UR, i, j + 1, k) - hrc<CIJ>(g, c, UR, i, j - 1, k)) * h * ir * g.idth;
+  R xrp = (hpc<CIJ>(g, c, UP, i + 1, j, k) - hpc<CIJ>(g, c, UP, i - 1, j, k)) * h * g.idr
+        + (hrc<CIJ>(g, c, UR, i, j, k + 1) - hrc<CIJ>(g, c, UR, i, j, k - 1)) * h * ir * is * g.idph;
+  R xtp = (hpc<CIJ>(g, c, UP, i, j + 1, k) - hpc<CIJ>(g, c, UP, i, j - 1, k)) * h * ir * g.idth
+        + (htc<CIJ>(g, c, UT, i, j, k + 1) - htc<CIJ>(g, c, UT, i, j, k - 1)) * h * ir * is * g.idph;
   R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
   accp += -mu * (gm - R(1)) * cross;
   accT += -mu * c.beta[t] * cross;
@@ -280,8 +280,8 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     // D_M
     R irf = g.irf[i], s = g.sc[j], is = g.isc[j];
     R irh = sdiv(R(2), rs);
-    R utf = h * (ht<CIJ>(g, UT, i - 1, j, k) + ht<CIJ>(g, UT, i, j, k));
-    R upf = h * (hp<CIJ>(g, UP, i - 1, j, k) + hp<CIJ>(g, UP, i, j, k));
+    R utf = h * (htc<CIJ>(g, c, UT, i - 1, j, k) + htc<CIJ>(g, c, UT, i, j, k));
+    R upf = h * (hpc<CIJ>(g, c, UP, i - 1, j, k) + hpc<CIJ>(g, c, UP, i, j, k));
     R Q[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
@@ -303,8 +303,8 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     R isfj = g.isf[j], cfj = g.cf[j], cotf = g.cotf[j];
     R irh = sdiv(R(2), rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
     R ubt = UT[t];
-    R upf = h * (hp<CIJ>(g, UP, i, j - 1, k) + hp<CIJ>(g, UP, i, j, k));
-    R vrf = h * (hr<CIJ>(g, UR, i, j - 1, k) + hr<CIJ>(g, UR, i, j, k));
+    R upf = h * (hpc<CIJ>(g, c, UP, i, j - 1, k) + hpc<CIJ>(g, c, UP, i, j, k));
+    R vrf = h * (hrc<CIJ>(g, c, UR, i, j - 1, k) + hrc<CIJ>(g, c, UR, i, j, k));
     R Dr[2], Dp[2], dpf = R(0);
 #pragma unroll
     for (int q = 0; q < 2; q++) {
@@ -317,7 +317,7 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     }
     acc += ubt * vrf * ir - upf * upf * cotf * ir + mu * irh * ubt * ir * ir * isfj * isfj - R(2) * om * cfj * upf
          - mu * irh * R(1.0 / 3.0) * ir * g.idth * ((Dr[1] - Dr[0]) + (Dp[1] - Dp[0]))
-         - mu * irh * (R(2) * ir * ir * g.idth * (hr<CIJ>(g, UR, i, j, k) - hr<CIJ>(g, UR, i, j - 1, k))
+         - mu * irh * (R(2) * ir * ir * g.idth * (hrc<CIJ>(g, c, UR, i, j, k) - hrc<CIJ>(g, c, UR, i, j - 1, k))
                        - R(2) * cfj * ir * ir * isfj * isfj * dpf);
   } else {
     R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
@@ -331,8 +331,8 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     R s = g.sc[j], cj = g.cc[j];
     R irh = sdiv(R(2), rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
     R ubp = UP[t];
-    R vrf = h * (hr<CIJ>(g, UR, i, j, k - 1) + hr<CIJ>(g, UR, i, j, k));
-    R vtf = h * (ht<CIJ>(g, UT, i, j, k - 1) + ht<CIJ>(g, UT, i, j, k));
+    R vrf = h * (hrc<CIJ>(g, c, UR, i, j, k - 1) + hrc<CIJ>(g, c, UR, i, j, k));
+    R vtf = h * (htc<CIJ>(g, c, UT, i, j, k - 1) + htc<CIJ>(g, c, UT, i, j, k));
     R Dr[2], Dt[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
@@ -343,8 +343,8 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     }
     acc += ubp * vtf * cot * ir + ubp * vrf * ir + mu * irh * ubp * ir * ir * is * is + R(2) * om * (cj * vtf + s * vrf)
          - mu * irh * R(1.0 / 3.0) * ir * is * g.idph * ((Dr[1] - Dr[0]) + (Dt[1] - Dt[0]))
-         - mu * irh * (R(2) * ir * ir * is * g.idph * (hr<CIJ>(g, UR, i, j, k) - hr<CIJ>(g, UR, i, j, k - 1))
-                       + R(2) * cj * ir * ir * is * is * g.idph * (ht<CIJ>(g, UT, i, j, k) - ht<CIJ>(g, UT, i, j, k - 1)));
+         - mu * irh * (R(2) * ir * ir * is * g.idph * (hrc<CIJ>(g, c, UR, i, j, k) - hrc<CIJ>(g, c, UR, i, j, k - 1))
+                       + R(2) * cj * ir * ir * is * is * g.idph * (htc<CIJ>(g, c, UT, i, j, k) - htc<CIJ>(g, c, UT, i, j, k - 1)));
   }
   if (has_src) acc -= to_bulk<R>(src.f[1 + D][t]);
   R dd = hasD ? Dv.f[1 + D][t] : R(0);

@@ -216,10 +216,58 @@ __device__ __forceinline__ R rho_at(const Geo<R>& g, const Coef<R>& c, int i, in
   return c.rho[IC(g, i, j, k)];
 }
 
+// A velocity component averaged to centre (i, j, k): in interior blocks
+// (CIJ = false) read from the coefficient plane k_coef wrote (uc0/uc1/uc2, the
+// same FP32 operations, so the same value), with the no-slip ghost -- minus the
+// mirrored centre -- beyond a phi wall and the periodic wrap (only used for
+// components tangential to phi); elsewhere the face average with all checks.
+template <typename R>
+__device__ __forceinline__ R ucen(const Geo<R>& g, const R* plane, int i, int j, int k) {
+  if (k < 0 || k >= g.np) {
+    if (g.per) k = wrapk(g, k);
+    else return -plane[IC(g, i, j, k < 0 ? 0 : g.np - 1)];
+  }
+  return plane[IC(g, i, j, k)];
+}
+template <bool CIJ, typename R>
+__device__ __forceinline__ R hrc(const Geo<R>& g, const Coef<R>& c, const R* u, int i, int j, int k) {
+  if constexpr (CIJ) return hr<true>(g, u, i, j, k);
+  else return ucen(g, (const R*)c.uc0, i, j, k);
+}
+template <bool CIJ, typename R>
+__device__ __forceinline__ R htc(const Geo<R>& g, const Coef<R>& c, const R* u, int i, int j, int k) {
+  if constexpr (CIJ) return ht<true>(g, u, i, j, k);
+  else return ucen(g, (const R*)c.uc1, i, j, k);
+}
+template <bool CIJ, typename R>
+__device__ __forceinline__ R hpc(const Geo<R>& g, const Coef<R>& c, const R* u, int i, int j, int k) {
+  if constexpr (CIJ) return hp<true>(g, u, i, j, k);
+  else return ucen(g, (const R*)c.uc2, i, j, k);
+}
+
 // whether the +-2 neighbourhood of (i, j) in r and theta is inside the grid
 template <typename G>
 __device__ __forceinline__ bool inner_ij(const G& g, int i, int j) {
   return i >= 2 && i <= g.nr - 3 && j >= 2 && j <= g.nt - 3;
+}
+
+// --------------------------------------------------------- thermodynamics
+// Coefficients of a centre from the midpoint perturbations p', T' and the
+// background at radius index i; k_coef and the line kernels both call this, so
+// their values are the same.
+template <typename R>
+struct Thermo { R Pb, Tb, rho, beta; };
+template <typename R>
+__device__ __forceinline__ Thermo<R> thermo(const Geo<R>& g, const Par& P, int i, R pp, R Tp) {
+  R pref = g.pcen[i], Tref = g.Tcen[i];
+  Thermo<R> t;
+  t.Pb = pref + pp;
+  t.Tb = Tref + Tp;
+  R iRg = pick<R>(1.0 / P.Rg, P.iRg_f);
+  R itb = sdiv(R(1), t.Tb);
+  t.rho = t.Pb * itb * iRg;
+  t.beta = sdiv((pick<R>(P.gamma, P.gamma_f) - R(1)) * t.Tb, t.Pb);
+  return t;
 }
 
 // ------------------------------------------------------------------- rows
@@ -397,12 +445,12 @@ __device__ __forceinline__ SPt<R> load_s(const Geo<R>& g, const Coef<R>& c, cons
   if (cc == 0) { q.rho0 = rho_at(g, c, i - 1, j, k); q.rho1 = rho_at(g, c, i, j, k); }
   else if (cc == 1) { q.rho0 = rho_at(g, c, i, j - 1, k); q.rho1 = rho_at(g, c, i, j, k); }
   else { q.rho0 = rho_at(g, c, i, j, k - 1); q.rho1 = rho_at(g, c, i, j, k); }
-  if (cc == 0) q.ua = d == 1 ? R(0.5) * (ht<CIJ>(g, ub.f[2], i - 1, j, k) + ht<CIJ>(g, ub.f[2], i, j, k))
-                             : R(0.5) * (hp<CIJ>(g, ub.f[3], i - 1, j, k) + hp<CIJ>(g, ub.f[3], i, j, k));
-  else if (cc == 1) q.ua = d == 0 ? R(0.5) * (hr<CIJ>(g, ub.f[1], i, j - 1, k) + hr<CIJ>(g, ub.f[1], i, j, k))
-                                  : R(0.5) * (hp<CIJ>(g, ub.f[3], i, j - 1, k) + hp<CIJ>(g, ub.f[3], i, j, k));
-  else q.ua = d == 0 ? R(0.5) * (hr<CIJ>(g, ub.f[1], i, j, k - 1) + hr<CIJ>(g, ub.f[1], i, j, k))
-                     : R(0.5) * (ht<CIJ>(g, ub.f[2], i, j, k - 1) + ht<CIJ>(g, ub.f[2], i, j, k));
+  if (cc == 0) q.ua = d == 1 ? R(0.5) * (htc<CIJ>(g, c, ub.f[2], i - 1, j, k) + htc<CIJ>(g, c, ub.f[2], i, j, k))
+                             : R(0.5) * (hpc<CIJ>(g, c, ub.f[3], i - 1, j, k) + hpc<CIJ>(g, c, ub.f[3], i, j, k));
+  else if (cc == 1) q.ua = d == 0 ? R(0.5) * (hrc<CIJ>(g, c, ub.f[1], i, j - 1, k) + hrc<CIJ>(g, c, ub.f[1], i, j, k))
+                                  : R(0.5) * (hpc<CIJ>(g, c, ub.f[3], i, j - 1, k) + hpc<CIJ>(g, c, ub.f[3], i, j, k));
+  else q.ua = d == 0 ? R(0.5) * (hrc<CIJ>(g, c, ub.f[1], i, j, k - 1) + hrc<CIJ>(g, c, ub.f[1], i, j, k))
+                     : R(0.5) * (htc<CIJ>(g, c, ub.f[2], i, j, k - 1) + htc<CIJ>(g, c, ub.f[2], i, j, k));
   return q;
 }
 

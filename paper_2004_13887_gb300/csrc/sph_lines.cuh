@@ -40,7 +40,7 @@ namespace lines {
 
 constexpr int LS = 33;        // shared-memory stride of one lane's chunk: 32 values + 1 pad
 constexpr int FS = 32 * LS;   // shared-memory stride of one staged field
-constexpr int NFB = 15;       // staged fields of a block line
+constexpr int NFB = 11;       // staged fields of a block line
 constexpr int NFS = 4;        // staged fields of a scalar line
 constexpr int NFAC = 21;      // E (9), g (3), H (9) per interior cell
 constexpr int NR3 = 21;       // a normalised reduced row: A (0-8), C (9-17), r (18-20)
@@ -184,9 +184,10 @@ __device__ __forceinline__ void cpa_wait_all() {
 }
 
 // stage the inputs of block-line cell c of line (a, b) at shared index si:
-// the centre coefficients, rho on both sides of face c+1, Ubar's u_D there and
-// the three right-hand-side values (a line's last face of a walled line has no
-// row: constants)
+// Ubar's p' and T' (the thermodynamic coefficients follow from them), the
+// velocity-gradient coefficients, Ubar's u_D on face c+1 (the centre velocity
+// is the mean of the cell's two faces) and the three right-hand-side values
+// (the last face of a walled line has no row: zero)
 template <int D>
 __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c, int n,
                                             int cyc) {
@@ -195,26 +196,18 @@ __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm
   int i, j, k;
   line_pos(D, a, b, c, i, j, k);
   int ic = IC(g, i, j, k);
-  cpa4(sm + 0 * FS + si, C.Pb + ic); cpa4(sm + 1 * FS + si, C.Tb + ic); cpa4(sm + 2 * FS + si, C.beta + ic);
-  cpa4(sm + 3 * FS + si, (D == 0 ? C.uc0 : D == 1 ? C.uc1 : C.uc2) + ic);
-  cpa4(sm + 4 * FS + si, C.grr + ic); cpa4(sm + 5 * FS + si, C.gtt + ic); cpa4(sm + 6 * FS + si, C.gpp + ic);
-  if (D == 1) { cpa4(sm + 7 * FS + si, C.srt + ic); sm[8 * FS + si] = 0.f; }
-  if (D == 2) { cpa4(sm + 7 * FS + si, C.srp + ic); cpa4(sm + 8 * FS + si, C.stp + ic); }
-  if (c < n - 1 || cyc) {
-    int fi, fj, fk;
-    next_face(D, n, c, i, j, k, fi, fj, fk);
-    int f = face_idx(g, D, fi, fj, fk);
-    // rho at the centres on both sides of the face (the cell and the next one along D)
-    int in = D == 0 ? IC(g, fi, j, k) : D == 1 ? IC(g, i, fj, k) : IC(g, i, j, fk);
-    cpa4(sm + 9 * FS + si, C.rho + ic);
-    cpa4(sm + 10 * FS + si, C.rho + in);
-    cpa4(sm + 11 * FS + si, S.ub.f[1 + D] + f);
-    cpa4(sm + 14 * FS + si, S.rhs.f[1 + D] + f);
-  } else {
-    sm[9 * FS + si] = 1.f; sm[10 * FS + si] = 1.f; sm[11 * FS + si] = 0.f; sm[14 * FS + si] = 0.f;
-  }
-  cpa4(sm + 12 * FS + si, S.rhs.f[0] + ic);
-  cpa4(sm + 13 * FS + si, S.rhs.f[4] + ic);
+  cpa4(sm + 0 * FS + si, S.ub.f[0] + ic); cpa4(sm + 1 * FS + si, S.ub.f[4] + ic);
+  cpa4(sm + 2 * FS + si, C.grr + ic); cpa4(sm + 3 * FS + si, C.gtt + ic); cpa4(sm + 4 * FS + si, C.gpp + ic);
+  if (D == 1) { cpa4(sm + 5 * FS + si, C.srt + ic); sm[6 * FS + si] = 0.f; }
+  if (D == 2) { cpa4(sm + 5 * FS + si, C.srp + ic); cpa4(sm + 6 * FS + si, C.stp + ic); }
+  int fi, fj, fk;
+  next_face(D, n, c, i, j, k, fi, fj, fk);
+  int f = face_idx(g, D, fi, fj, fk);
+  cpa4(sm + 7 * FS + si, S.ub.f[1 + D] + f);
+  if (c < n - 1 || cyc) cpa4(sm + 10 * FS + si, S.rhs.f[1 + D] + f);
+  else sm[10 * FS + si] = 0.f;
+  cpa4(sm + 8 * FS + si, S.rhs.f[0] + ic);
+  cpa4(sm + 9 * FS + si, S.rhs.f[4] + ic);
 }
 
 // stage the inputs of scalar-line cell c (component cc) of line (a, b)
@@ -259,7 +252,7 @@ __device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, float* ss
 
 // Block lines (p, T, u_D) of direction D, n = 32 P cells per line.
 template <int D, int P>
-__global__ void __launch_bounds__(1024 / P, P == 8 ? 3 : P == 4 ? 2 : 1) k_lines_blk(SweepArgs<float> S) {
+__global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines_blk(SweepArgs<float> S) {
   constexpr int NW = 32 / P;
   constexpr int NT = 32 * NW;
   extern __shared__ float sm[];
@@ -286,20 +279,50 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 3 : P == 4 ? 2 : 1) k_lines
     float Xs[NR3];  // the separator row: lower (0-8), C (9-17), r (18-20); diagonal in Bs
     float Bs[9];
     int a = G.a, b = G.bb + w;
+    // the cell before the chunk's first: Ubar's u_D on the chunk's first face
+    // (the wall value at the start of a walled line)
+    float uf;
+    {
+      int m0 = lane * P;
+      if (m0 > 0 || cyc) {
+        uf = sm[7 * FS + sidx<P>(w, m0 > 0 ? m0 - 1 : n - 1)];
+      } else {
+        int i, j, k;
+        line_pos(D, a, b, 0, i, j, k);
+        uf = S.ub.f[1 + D][face_idx(g, D, i, j, k)];
+      }
+    }
+    Thermo<float> th;
+    {
+      int i, j, k, m0 = lane * P, s0 = sidx<P>(w, m0);
+      line_pos(D, a, b, m0, i, j, k);
+      th = thermo(g, S.P, i, sm[s0], sm[FS + s0]);
+    }
 #pragma unroll 1
     for (int t = 0; t < P; t++) {
       int m = lane * P + t;
       int si = sidx<P>(w, m);
-      CPt<float> cq;
-      cq.Pb = sm[0 * FS + si]; cq.Tb = sm[1 * FS + si]; cq.beta = sm[2 * FS + si]; cq.uc = sm[3 * FS + si];
-      cq.grr = sm[4 * FS + si]; cq.gtt = sm[5 * FS + si]; cq.gpp = sm[6 * FS + si];
-      cq.s1 = D > 0 ? sm[7 * FS + si] : 0.f;
-      cq.s2 = D > 0 ? sm[8 * FS + si] : 0.f;
-      FPt<float> fq = {sm[9 * FS + si], sm[10 * FS + si], sm[11 * FS + si]};
-      float rr[3] = {sm[12 * FS + si], sm[13 * FS + si], sm[14 * FS + si]};
       int i, j, k, fi, fj, fk;
       line_pos(D, a, b, m, i, j, k);
       next_face(D, n, m, i, j, k, fi, fj, fk);
+      float ufn = sm[7 * FS + si];
+      CPt<float> cq;
+      cq.Pb = th.Pb; cq.Tb = th.Tb; cq.beta = th.beta;
+      cq.uc = 0.5f * (uf + ufn);
+      cq.grr = sm[2 * FS + si]; cq.gtt = sm[3 * FS + si]; cq.gpp = sm[4 * FS + si];
+      cq.s1 = D > 0 ? sm[5 * FS + si] : 0.f;
+      cq.s2 = D > 0 ? sm[6 * FS + si] : 0.f;
+      FPt<float> fq = {th.rho, 1.f, ufn};
+      if (m < n - 1 || cyc) {
+        // the next cell along the line: its thermodynamics serve this face row and the next step
+        int mn = m + 1 == n ? 0 : m + 1, sn = sidx<P>(w, mn);
+        int in_, jn, kn;
+        line_pos(D, a, b, mn, in_, jn, kn);
+        th = thermo(g, S.P, in_, sm[sn], sm[FS + sn]);
+        fq.rho1 = th.rho;
+      }
+      uf = ufn;
+      float rr[3] = {sm[8 * FS + si], sm[9 * FS + si], sm[10 * FS + si]};
       float A[9], B[9], C[9];
       assemble_pts(g, S.P, cq, fq, D, n, cyc, m, i, j, fi, fj, h, A, B, C);
       if (t < P - 1) {
