@@ -211,15 +211,18 @@ def bubble_window(n=(128, 256, 256), width=(64, 64)) -> Grid:
 
 def bubble(n=(128, 256, 256), seed: int = 1, dt: float = 1.0, steps: int = 200, K: int = 2,
            amplitude: float = 0.5, radius: float = 2000.0, altitude: float = 2000.0, mu: float = None,
-           grid: Grid = None) -> Case:
-    """Rising thermal bubble: Gaussian dTheta = A exp(-L^2), L = |x - x_c| / R,
-    centre at the given altitude above the domain centre, centre altitude and
-    radius jittered by +-10 % (seeded).  grid: another grid (e.g. a central
-    window of the sector) to sample the same initial state on."""
+           grid: Grid = None, profile: str = "gaussian", jitter: bool = True) -> Case:
+    """Rising thermal bubble: dTheta = A f(L), L = |x - x_c| / R, centre at the
+    given altitude above the domain centre.  profile "gaussian": f = exp(-L^2)
+    (the benchmark workload; centre altitude and radius jittered by +-10 %,
+    seeded); "cos2": f = cos^2(pi L / 2) for L <= 1 (Thermal 1, eq. temp_pert);
+    "cos": f = (1 + cos(pi L)) / 2 for L <= 1 (Thermal 2).  grid: another grid
+    (e.g. a central window of the sector) to sample the same initial state on."""
     grid = bubble_grid(n) if grid is None else grid
     rng = np.random.default_rng(seed)
-    radius = radius * (1.0 + rng.uniform(-0.1, 0.1))
-    altitude = altitude * (1.0 + rng.uniform(-0.1, 0.1))
+    if jitter:
+        radius = radius * (1.0 + rng.uniform(-0.1, 0.1))
+        altitude = altitude * (1.0 + rng.uniform(-0.1, 0.1))
     par = Params(gamma=AIR["cp"] / AIR["cv"], cv=AIR["cv"], Pr=AIR["Pr"],
                  mu=AIR["mu"] if mu is None else mu, g=AIR["g"])
     bgp, bgT, Pi = hydrostatic_background(grid, cp=AIR["cp"], cv=AIR["cv"], g=AIR["g"])
@@ -231,11 +234,46 @@ def bubble(n=(128, 256, 256), seed: int = 1, dt: float = 1.0, steps: int = 200, 
     y = R * np.sin(TH) * np.sin(PH) - rcen * math.sin(tc) * math.sin(pc)
     z = R * np.cos(TH) - rcen * math.cos(tc)
     L2 = (x * x + y * y + z * z) / radius ** 2
-    dtheta = amplitude * np.exp(-L2)
+    if profile == "gaussian":
+        dtheta = amplitude * np.exp(-L2)
+    elif profile == "cos2":
+        L = np.sqrt(L2)
+        dtheta = np.where(L <= 1.0, amplitude * np.cos(0.5 * math.pi * L) ** 2, 0.0)
+    elif profile == "cos":
+        L = np.sqrt(L2)
+        dtheta = np.where(L <= 1.0, amplitude * 0.5 * (1.0 + np.cos(math.pi * L)), 0.0)
+    else:
+        raise ValueError(profile)
     Pic = Pi[1:-1][:, None, None]
     U[4] = np.ascontiguousarray(np.broadcast_to(Pic * dtheta, grid.shapes()[4]))
     return Case("bubble", grid, par, dt, steps, K, (bgp, bgT), U,
                 info=dict(seed=seed, radius=radius, altitude=altitude, amplitude=amplitude))
+
+
+def thermal1(n=(100, 200, 200), dt: float = 1.0, mu: float = None, K: int = 2) -> Case:
+    """Section 3.2, Thermal 1: the 10 km x 20 km x 20 km sector, dTheta =
+    2 cos^2(pi L / 2) for L <= 1 (L normalised by R = 2 km, reading R13), centre
+    2 km above the bottom on the sector axis; dry air, t_end = 500 s."""
+    c = bubble(n, dt=dt, K=K, amplitude=2.0, radius=2000.0, altitude=2000.0, mu=mu, profile="cos2", jitter=False)
+    c.info["t_end"] = 500.0
+    return c
+
+
+def thermal2_grid(n=(200, 200, 200)) -> Grid:
+    """Section 3.2, Thermal 2 domain: r in [6371, 6372] km (reading R14), theta
+    and phi within 0.5 km / 6371 km of the equator and of phi = pi."""
+    half = 0.5 / 6371.0
+    return Grid(n[0], n[1], n[2], 6371e3, 6372e3, math.pi / 2 - half, math.pi / 2 + half,
+                math.pi - half, math.pi + half)
+
+
+def thermal2(n=(200, 200, 200), dt: float = 1.0, K: int = 2) -> Case:
+    """Section 3.2, Thermal 2: the 1 km box, dTheta = (1 + cos(pi L)) / 4 for
+    L <= 1, R = 250 m, centre 260 m above the bottom; t_end = 400 s."""
+    g = thermal2_grid(n)
+    c = bubble(n, dt=dt, K=K, amplitude=0.5, radius=250.0, altitude=260.0, profile="cos", jitter=False, grid=g)
+    c.info["t_end"] = 400.0
+    return c
 
 
 ENSEMBLE_SEED = 20041389

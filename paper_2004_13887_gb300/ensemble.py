@@ -43,7 +43,7 @@ def autotune(cases, dt, n_iter):
         for which in (SPH_LINES_PARTITIONED, SPH_LINES_THOMAS):
             s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
             s.set_background(*c.bg)
-            s.set_state([torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in c.init])
+            s.set_state([torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init])
             s.set_line_solver(which)
             ms = time_steps(s, dt, n_iter)
             s.close()
@@ -67,7 +67,7 @@ class Ensemble:
         for c in self.cases:
             s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
             s.set_background(*c.bg)
-            s.set_state([torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in c.init])
+            s.set_state([torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init])
             shape = (c.grid.nr, c.grid.nt, c.grid.np)
             if shape in self.choice:
                 s.set_line_solver(self.choice[shape])

@@ -18,7 +18,7 @@ def to_host(fields):
 
 def to_dev(fields):
     import torch
-    return [torch.from_numpy(np.ascontiguousarray(f)).to("cuda") for f in fields]
+    return [torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).to("cuda") for f in fields]
 
 
 def solver_for(grid, par, bg=None, state=None, precision=0):
