@@ -75,6 +75,46 @@ __device__ __forceinline__ void mv3(const float* X, const float* y, float* z) {
   for (int r = 0; r < 3; r++) z[r] = X[r * 3] * y[0] + X[r * 3 + 1] * y[1] + X[r * 3 + 2] * y[2];
 }
 
+// Products with the two sparse blocks of a line row.  The lower block A is
+// upper triangular (A[3] = A[6] = A[7] = 0: the T row does not see p_{m-1} and
+// the u row sees only u on face m); the upper block C has C[2] = C[3] = C[5] =
+// C[7] = 0 (the p and T rows see u only on the cell's own faces, the T row no
+// p_{m+1}, the u row no T_{m+1}).  Boundary folding only zeroes more entries.
+__device__ __forceinline__ void mm3_A(const float* A, const float* Y, float* Z) {  // A Y
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    Z[q] = A[0] * Y[q] + A[1] * Y[3 + q] + A[2] * Y[6 + q];
+    Z[3 + q] = A[4] * Y[3 + q] + A[5] * Y[6 + q];
+    Z[6 + q] = A[8] * Y[6 + q];
+  }
+}
+__device__ __forceinline__ void mv3_A(const float* A, const float* y, float* z) {
+  z[0] = A[0] * y[0] + A[1] * y[1] + A[2] * y[2];
+  z[1] = A[4] * y[1] + A[5] * y[2];
+  z[2] = A[8] * y[2];
+}
+__device__ __forceinline__ void mm3_C(const float* C, const float* Y, float* Z) {  // C Y
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    Z[q] = C[0] * Y[q] + C[1] * Y[3 + q];
+    Z[3 + q] = C[4] * Y[3 + q];
+    Z[6 + q] = C[6] * Y[q] + C[8] * Y[6 + q];
+  }
+}
+__device__ __forceinline__ void mv3_C(const float* C, const float* y, float* z) {
+  z[0] = C[0] * y[0] + C[1] * y[1];
+  z[1] = C[4] * y[1];
+  z[2] = C[6] * y[0] + C[8] * y[2];
+}
+__device__ __forceinline__ void mm3_XC(const float* X, const float* C, float* Z) {  // X C
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+    Z[r * 3] = X[r * 3] * C[0] + X[r * 3 + 2] * C[6];
+    Z[r * 3 + 1] = X[r * 3] * C[1] + X[r * 3 + 1] * C[4];
+    Z[r * 3 + 2] = X[r * 3 + 2] * C[8];
+  }
+}
+
 template <int NS>
 __device__ __forceinline__ void shfl_get(const float* s, float* o, int src, bool zero) {
 #pragma unroll
@@ -210,14 +250,17 @@ __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm
   cpa4(sm + 9 * FS + si, S.rhs.f[4] + ic);
 }
 
-// stage the inputs of scalar-line cell c (component cc) of line (a, b)
+// stage the inputs of scalar-line cell c (component cc) of line (a, b); away
+// from the r and theta walls the averaged velocities come from the coefficient
+// planes without checks
 template <int D, int KIND>
 __device__ __forceinline__ void stage_scalar(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c) {
   const Geo<float>& g = S.g;
   constexpr int cc = trans_comp(D, KIND);
   int i, j, k;
   line_pos(D, a, b, c, i, j, k);
-  SPt<float> q = load_s(g, S.c, S.ub, cc, D, i, j, k);
+  SPt<float> q = inner_ij(g, i, j) ? load_s<false>(g, S.c, S.ub, cc, D, i, j, k)
+                                   : load_s<true>(g, S.c, S.ub, cc, D, i, j, k);
   sm[0 * FS + si] = q.rho0; sm[1 * FS + si] = q.rho1; sm[2 * FS + si] = q.ua;
   sm[3 * FS + si] = S.rhs.f[1 + cc][face_idx(g, cc, i, j, k)];
 }
@@ -334,18 +377,18 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
           for (int q = 0; q < 3; q++) rv[q] = rr[q];
         } else {
           float T9[9], u[3];
-          mm3(A, E, T9);
+          mm3_A(A, E, T9);
 #pragma unroll
           for (int q = 0; q < 9; q++) Sm[q] = B[q] - T9[q];
-          mv3(A, gg, u);
+          mv3_A(A, gg, u);
 #pragma unroll
           for (int q = 0; q < 3; q++) rv[q] = rr[q] - u[q];
-          mm3(A, H, T9);
+          mm3_A(A, H, T9);
 #pragma unroll
           for (int q = 0; q < 9; q++) Hs[q] = -T9[q];
         }
         if (!inv3(Sm, Si)) bad |= FLAG_SINGULAR;
-        mm3(Si, C, E);
+        mm3_XC(Si, C, E);
         mv3(Si, rv, gg);
         mm3(Si, Hs, H);
         float* s = slot + t * NFAC * 32 + lane;
@@ -363,13 +406,13 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       } else {
         // separator: x_{s-1} = g - E X_l - H X_{l-1}
         float T9[9], u[3];
-        mm3(A, H, T9);
+        mm3_A(A, H, T9);
 #pragma unroll
         for (int q = 0; q < 9; q++) Xs[q] = -T9[q];
-        mm3(A, E, T9);
+        mm3_A(A, E, T9);
 #pragma unroll
         for (int q = 0; q < 9; q++) { Bs[q] = B[q] - T9[q]; Xs[9 + q] = C[q]; }
-        mv3(A, gg, u);
+        mv3_A(A, gg, u);
 #pragma unroll
         for (int q = 0; q < 3; q++) Xs[18 + q] = rr[q] - u[q];
       }
@@ -407,13 +450,13 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       shfl_get<3>(p, pn, (lane + 1) & 31, none);
       shfl_get<9>(Q, Qn, (lane + 1) & 31, none);
       shfl_get<9>(W, Wn, (lane + 1) & 31, none);
-      mm3(Xs + 9, Wn, T9);
+      mm3_C(Xs + 9, Wn, T9);
 #pragma unroll
       for (int q = 0; q < 9; q++) Bs[q] += T9[q];
-      mv3(Xs + 9, pn, u);
+      mv3_C(Xs + 9, pn, u);
 #pragma unroll
       for (int q = 0; q < 3; q++) Xs[18 + q] -= u[q];
-      mm3(Xs + 9, Qn, T9);
+      mm3_C(Xs + 9, Qn, T9);
 #pragma unroll
       for (int q = 0; q < 9; q++) Xs[9 + q] = T9[q];
     }
