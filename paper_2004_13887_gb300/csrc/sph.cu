@@ -132,13 +132,37 @@ __device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<
   c.stp[t] = gtp + gpt;
 }
 
-// one block per (i, j) row of 128 phi-consecutive centres
+// The stencil kernels run on tiles of TK x TJ x TI points (phi fastest; 128
+// threads).  A block takes the fast path when its whole tile has its +-2
+// neighbourhood in r and theta inside the grid (a uniform choice).  On the
+// 128 x 256 x 256 workload the tile shape made no measurable difference
+// (128x1x1 to 16x4x2 all within 3 %), so the default is one phi row.
+#ifndef SPH_TILE_J
+#define SPH_TILE_J 1
+#endif
+#ifndef SPH_TILE_I
+#define SPH_TILE_I 1
+#endif
+constexpr int TILE_K = 128 / (SPH_TILE_J * SPH_TILE_I), TILE_J = SPH_TILE_J, TILE_I = SPH_TILE_I;
+template <typename G>
+__device__ __forceinline__ bool tile_inner(const G& g) {
+  int i0 = blockIdx.z * blockDim.z, j0 = blockIdx.y * blockDim.y;
+  return inner_ij(g, i0, j0) && inner_ij(g, i0 + (int)blockDim.z - 1, j0 + (int)blockDim.y - 1);
+}
+static dim3 tile_grid(int nk, int nj, int ni) {
+  return dim3((nk + TILE_K - 1) / TILE_K, (nj + TILE_J - 1) / TILE_J, (ni + TILE_I - 1) / TILE_I);
+}
+static const dim3 TILE_BLOCK(TILE_K, TILE_J, TILE_I);
+
+// one block per tile
 template <typename R>
 __global__ void __launch_bounds__(128) k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= g.np) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+      i = blockIdx.z * blockDim.z + threadIdx.z;
+  bool inner = tile_inner(g);
+  if (k >= g.np || j >= g.nt || i >= g.nr) return;
   int t = IC(g, i, j, k);
-  if (inner_ij(g, i, j)) coef_at<false>(g, P, ub, c, i, j, k, t);
+  if (inner) coef_at<false>(g, P, ub, c, i, j, k, t);
   else coef_at<true>(g, P, ub, c, i, j, k, t);
 }
 
@@ -242,15 +266,17 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
   Rout.f[4][t] = -d4 - tau * NT;
 }
 
-// one block per (i, j) row of 128 phi-consecutive centres
+// one block per tile
 template <typename R>
 __global__ void __launch_bounds__(128) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
                                                CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
                                                int has_src, R tau, MF<R> Rout) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= g.np) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+      i = blockIdx.z * blockDim.z + threadIdx.z;
+  bool inner = tile_inner(g);
+  if (k >= g.np || j >= g.nt || i >= g.nr) return;
   int t = IC(g, i, j, k);
-  if (inner_ij(g, i, j)) rhs_c_at<false>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+  if (inner) rhs_c_at<false>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
   else rhs_c_at<true>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
 }
 
@@ -351,18 +377,19 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
   Rout.f[1 + D][t] = -dd - tau * acc;
 }
 
-// one block per (i, j) row of 128 phi-consecutive faces; zero on wall faces,
-// which are not unknowns
+// one block per tile of faces; zero on wall faces, which are not unknowns
 template <typename R, int D>
 __global__ void __launch_bounds__(128) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<R> Dv, int hasD,
                                                CF<double> src, int has_src, R tau, MF<R> Rout) {
   int nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
-  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
-  if (k >= nk) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+      i = blockIdx.z * blockDim.z + threadIdx.z;
+  bool inner = tile_inner(g);
+  if (k >= nk || j >= nj || i >= g.nr + (D == 0)) return;
   int t = (i * nj + j) * nk + k;
   bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
   if (wall) { Rout.f[1 + D][t] = R(0); return; }
-  if (inner_ij(g, i, j)) rhs_u_at<false, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+  if (inner) rhs_u_at<false, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
   else rhs_u_at<true, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
 }
 
@@ -1246,7 +1273,7 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
   }
   k_begin(c, SPH_K_COEF);
   const Geo<double>& gg = c->d64.g;
-  k_coef<R><<<dim3((gg.np + 127) / 128, gg.nt, gg.nr), 128, 0, c->st>>>(b.g, c->P, ub, b.c);
+  k_coef<R><<<tile_grid(gg.np, gg.nt, gg.nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, ub, b.c);
   if (launch_ok(c)) return SPH_ERR_CUDA;
   *ub_out = ub;
   return SPH_OK;
@@ -1264,11 +1291,11 @@ static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, do
   k_begin(c, SPH_K_RHS);
   const Geo<double>& gg = c->d64.g;
   int nr = gg.nr, nt = gg.nt, np = gg.np, npf = gg.npf;
-  k_rhs_c<R><<<dim3((np + 127) / 128, nt, nr), 128, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD, src,
+  k_rhs_c<R><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD, src,
                                                                 has_src, tr, Rout);
-  k_rhs_u<R, 0><<<dim3((np + 127) / 128, nt, nr + 1), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 1><<<dim3((np + 127) / 128, nt + 1, nr), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 2><<<dim3((npf + 127) / 128, nt, nr), 128, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 0><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 1><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 2><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
   c->launches += 3;  // launch_ok counts the fourth
   return launch_ok(c);
 }
