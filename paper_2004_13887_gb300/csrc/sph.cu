@@ -860,6 +860,8 @@ struct sph_ctx {
   long long kcount[SPH_NKERNELS];
   int cur_kind;
   int nsm;               // multiprocessors of the device
+  cudaStream_t aux[3];   // side streams for independent launches of one stage
+  cudaEvent_t efork, ejoin[3];
   int line_solver;       // SPH_LINES_* for the mixed path
   size_t nscr;           // floats in each bulk scratch buffer
 };
@@ -916,6 +918,11 @@ static void bufs_free(Bufs<R>& b) {
 
 static void free_all(sph_ctx* c) {
   prof_free(c);
+  for (int q = 0; q < 3; q++) {
+    if (c->aux[q]) cudaStreamDestroy(c->aux[q]);
+    if (c->ejoin[q]) cudaEventDestroy(c->ejoin[q]);
+  }
+  if (c->efork) cudaEventDestroy(c->efork);
   bufs_free(c->d64);
   bufs_free(c->d32);
   cudaFree(c->bg); cudaFree(c->acc); cudaFree(c->flag);
@@ -1136,6 +1143,12 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   free(zb); free(tb);
   if (err != SPH_OK) { free_all(c); free(c); return err; }
   if (mixed && (err = lines_prepare(c)) != SPH_OK) { free_all(c); free(c); return err; }
+  if (cudaEventCreateWithFlags(&c->efork, cudaEventDisableTiming) != cudaSuccess) err = SPH_ERR_CUDA;
+  for (int q = 0; q < 3 && !err; q++)
+    if (cudaStreamCreateWithFlags(&c->aux[q], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ejoin[q], cudaEventDisableTiming) != cudaSuccess)
+      err = SPH_ERR_CUDA;
+  if (err) { free_all(c); free(c); return err; }
   c->cur = 0;
   *out = c;
   return SPH_OK;
@@ -1279,8 +1292,26 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
   return SPH_OK;
 }
 
-// The right-hand side stage: centre rows, then the momentum rows of each
-// component (timed as one stage).
+// Independent launches of one stage run side by side: `fork` makes n side
+// streams wait for the work enqueued so far on the context's stream, `join`
+// makes the context's stream wait for them (both are stream-ordered, so a
+// CUDA graph capture follows them).
+static int fork_aux(sph_ctx* c, int n) {
+  if (cudaEventRecord(c->efork, c->st) != cudaSuccess) return SPH_ERR_CUDA;
+  for (int q = 0; q < n; q++)
+    if (cudaStreamWaitEvent(c->aux[q], c->efork, 0) != cudaSuccess) return SPH_ERR_CUDA;
+  return SPH_OK;
+}
+static int join_aux(sph_ctx* c, int n) {
+  for (int q = 0; q < n; q++)
+    if (cudaEventRecord(c->ejoin[q], c->aux[q]) != cudaSuccess || cudaStreamWaitEvent(c->st, c->ejoin[q], 0) != cudaSuccess)
+      return SPH_ERR_CUDA;
+  return SPH_OK;
+}
+
+// The right-hand side stage: centre rows on the context's stream, the
+// momentum rows of the three components on side streams, concurrently (timed
+// as one stage).
 template <typename R>
 static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, double tau, CF<double> src, int has_src,
                    MF<R> Rout) {
@@ -1289,13 +1320,15 @@ static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, do
   CF<R> ul = sizeof(R) == sizeof(float) ? cf_of(b.UbLo) : ub;  // velocity remainders of Ubar (FP32 mode)
   R tr = (R)tau;
   k_begin(c, SPH_K_RHS);
+  if (fork_aux(c, 3)) return SPH_ERR_CUDA;
   const Geo<double>& gg = c->d64.g;
   int nr = gg.nr, nt = gg.nt, np = gg.np, npf = gg.npf;
   k_rhs_c<R><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD, src,
                                                                 has_src, tr, Rout);
-  k_rhs_u<R, 0><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 1><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 2><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 0><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->aux[0]>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 1><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->aux[1]>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  k_rhs_u<R, 2><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->aux[2]>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  if (join_aux(c, 3)) return SPH_ERR_CUDA;
   c->launches += 3;  // launch_ok counts the fourth
   return launch_ok(c);
 }
@@ -1370,6 +1403,7 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
   int ng, e;
   k_begin(c, SPH_K_SWEEP_R + D);
   if ((e = lines_attr<D, P>())) return e;
+  if ((e = fork_aux(c, 2))) return e;
   if ((ng = lines_groups(S, 0, NW)) > 0) {
     // one factor slot per block
     if ((size_t)ng * NW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
@@ -1377,13 +1411,14 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
     c->launches++;
   }
   if ((ng = lines_groups(S, 1, NW)) > 0) {
-    lines::k_lines_sca<D, P, 1><<<ng, NT, sms, c->st>>>(S);
+    lines::k_lines_sca<D, P, 1><<<ng, NT, sms, c->aux[0]>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 2, NW)) > 0) {
-    lines::k_lines_sca<D, P, 2><<<ng, NT, sms, c->st>>>(S);
+    lines::k_lines_sca<D, P, 2><<<ng, NT, sms, c->aux[1]>>>(S);
     c->launches++;
   }
+  if ((e = join_aux(c, 2))) return e;
   c->launches--;  // launch_ok counts one more
   return launch_ok(c);
 }
