@@ -91,12 +91,18 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
 
     def start(self):
+        """start sampling every 20 ms and return once the first sample is in,
+        so that the timed region that follows is covered"""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.f.name) == 0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
