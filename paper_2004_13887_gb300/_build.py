@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsph.so")
 SOURCES = ["sph.cu", "sph_noalloc.cu"]
-HEADERS = ["sph_device.cuh"]
+HEADERS = ["sph_device.cuh", "sph_lines.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

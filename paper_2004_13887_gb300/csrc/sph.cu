@@ -47,8 +47,11 @@ using namespace sph;
 // FP32 mode both are formed as pairs on the FP32 pipe: o = Ubar rounded, and
 // for the velocity components lo[f] (when not null) = the remainder, so that
 // div(Ubar) can be formed to ~48 bits; D is rounded once from the exact pair.
+// same = 1 (the first iteration of a step, U^k = U^n): b is not read and D is
+// not written (the right-hand side does not read it then); Ubar = a is split
+// into its pair directly, which gives the same bits as (a + a)/2 in pairs.
 template <typename R>
-struct AvgArgs { const double* a[5]; const double* b[5]; R* o[5]; R* lo[5]; R* d[5]; long n[5]; };
+struct AvgArgs { const double* a[5]; const double* b[5]; R* o[5]; R* lo[5]; R* d[5]; long n[5]; int same; };
 
 template <typename R>
 __device__ __forceinline__ void avg1(const double x, const double y, R* o, R* lo, R* d, long t) {
@@ -68,6 +71,18 @@ __device__ __forceinline__ void avg1(const double x, const double y, R* o, R* lo
 }
 
 template <typename R>
+__device__ __forceinline__ void split1(const double x, R* o, R* lo, long t) {
+  if constexpr (sizeof(R) == sizeof(double)) {
+    o[t] = (R)x;
+  } else {
+    float h, l;
+    d2ff(x, h, l);
+    o[t] = h;
+    if (lo) lo[t] = l;
+  }
+}
+
+template <typename R>
 __global__ void k_avg(AvgArgs<R> A) {
   const int f = blockIdx.y;
   const double* __restrict__ a = A.a[f];
@@ -77,6 +92,15 @@ __global__ void k_avg(AvgArgs<R> A) {
   R* __restrict__ d = A.d[f];
   long n = A.n[f], n2 = n >> 1;
   long s = (long)gridDim.x * blockDim.x;
+  if (A.same) {
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += s) {
+      double2 x = reinterpret_cast<const double2*>(a)[t];
+      split1(x.x, o, lo, 2 * t);
+      split1(x.y, o, lo, 2 * t + 1);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) split1(a[n - 1], o, lo, n - 1);
+    return;
+  }
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += s) {
     double2 x = reinterpret_cast<const double2*>(a)[t], y = reinterpret_cast<const double2*>(b)[t];
     avg1(x.x, y.x, o, lo, d, 2 * t);
@@ -901,7 +925,8 @@ extern "C" const char* sph_strerror(int code) {
 }
 
 extern "C" int sph_set_line_solver(sph_ctx* ctx, int which) {
-  if (!ctx || (which != SPH_LINES_THOMAS && which != SPH_LINES_PARTITIONED)) return SPH_ERR_ARG;
+  if (!ctx || (which != SPH_LINES_THOMAS && which != SPH_LINES_PARTITIONED && which != SPH_LINES_PARTITIONED_WARP))
+    return SPH_ERR_ARG;
   ctx->line_solver = which;
   return SPH_OK;
 }
@@ -1064,6 +1089,7 @@ static int upload_background(sph_ctx* c, const double* pref, const double* Tref)
 }
 
 static int lines_prepare(const sph_ctx* c);
+static size_t lines_scratch(int nr, int nt, int np, int per);
 
 extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream, sph_ctx** out) {
   if (!gr || !pa || !out) return SPH_ERR_ARG;
@@ -1112,8 +1138,12 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
 
   size_t wblk = g.per ? 21 : 12;
   size_t nscr = (wblk + 6) * (size_t)c->N + 64;
-  // the partitioned solver's factor slots take up to 19.5 N floats
-  if (c->prec == SPH_PREC_MIXED && nscr < 20 * (size_t)c->N + 64) nscr = 20 * (size_t)c->N + 64;
+  // the partitioned solver's factor slots (up to 18.4 floats per cell, more
+  // where the lines of a launch's last group do not fill it)
+  if (c->prec == SPH_PREC_MIXED) {
+    size_t need = lines_scratch(g.nr, g.nt, g.np, g.per) + 64;
+    if (nscr < need) nscr = need;
+  }
   // kernels index with 32-bit ints: every array, and the scratch, must fit
   if (nscr >= (size_t)2147483647 || c->nf[1] >= (size_t)2147483647 || c->nf[3] >= (size_t)2147483647) {
     free(c->hmet); free(c); return SPH_ERR_ARG;
@@ -1279,6 +1309,7 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
     for (int f = 0; f < 5; f++) ub.f[f] = (const R*)un[f];
   } else {
     AvgArgs<R> A;
+    A.same = !have_iter;
     long mx = 0;
     for (int f = 0; f < 5; f++) {
       A.a[f] = un[f]; A.b[f] = uk[f]; A.o[f] = b.Ub[f]; A.lo[f] = b.UbLo[f]; A.d[f] = b.Db[f];
@@ -1372,17 +1403,18 @@ static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
   }
 }
 
-// Partitioned line solver (mixed path) for lines of n = 32 P cells: one
-// launch per line kind, one block per group of 32/P lines.
-// The shared-memory size attribute of the three kernels of a (D, P), set once
-// per process (at context creation, so that no attribute call falls inside a
-// CUDA graph capture).
-template <int D, int P>
+// Partitioned line solver (mixed path) for lines of n = L P cells, L lanes
+// per line: one launch per line kind, one block per group of 1024/n lines.
+// The shared-memory size attribute of the block-line kernel of a (D, P, L),
+// set once per process (at context creation, so that no attribute call falls
+// inside a CUDA graph capture).
+template <int D, int P, int L>
 static int lines_attr() {
   static int done = 0;
   if (done) return SPH_OK;
   const int smb = lines::NFB * lines::FS * (int)sizeof(float);
-  if (cudaFuncSetAttribute(lines::k_lines_blk<D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) != cudaSuccess)
+  if (cudaFuncSetAttribute(lines::k_lines_blk<D, P, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) !=
+      cudaSuccess)
     return SPH_ERR_CUDA;
   done = 1;
   return SPH_OK;
@@ -1394,6 +1426,29 @@ static int lines_groups(const SweepArgs<float>& S, int kind, int NW) {
   return na * ((nb + NW - 1) / NW);
 }
 
+// floats of factor slots the partitioned solver needs on a grid: the largest
+// over the directions it takes and the lane counts (16, 32) it may use there
+static size_t lines_scratch(int nr, int nt, int np, int per) {
+  Geo<double> g;
+  memset(&g, 0, sizeof g);
+  g.nr = nr; g.nt = nt; g.np = np; g.per = per;
+  size_t mx = 0;
+  for (int d = 0; d < 3; d++) {
+    int n = d == 0 ? nr : d == 1 ? nt : np;
+    if (n != 64 && n != 128 && n != 256) continue;
+    SweepArgs<float> S;
+    memset(&S, 0, sizeof S);
+    line_layout(g, d, S);
+    for (int L = 16; L <= 32; L += 16) {
+      if (L == 16 && n == 256) continue;
+      int P = n / L, NW = 1024 / n, NWW = 1024 / P / 32;
+      size_t need = (size_t)lines_groups(S, 0, NW) * NWW * 32 * lines::slot_floats(P);
+      if (need > mx) mx = need;
+    }
+  }
+  return mx;
+}
+
 // whether the partitioned solver can take the lines along d
 static int lines_ok(const sph_ctx* c, int d) {
   const Geo<double>& g = c->d64.g;
@@ -1401,27 +1456,28 @@ static int lines_ok(const sph_ctx* c, int d) {
   return n == 64 || n == 128 || n == 256;
 }
 
-template <int D, int P>
+template <int D, int P, int L>
 static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
-  constexpr int NW = 32 / P, NT = 32 * NW;
+  using SH = lines::Shape<P, L>;
+  constexpr int NW = SH::NW, NT = SH::NT;
   const size_t smb = (size_t)lines::NFB * lines::FS * sizeof(float);
   const size_t sms = (size_t)lines::NFS * lines::FS * sizeof(float);
   int ng, e;
   k_begin(c, SPH_K_SWEEP_R + D);
-  if ((e = lines_attr<D, P>())) return e;
+  if ((e = lines_attr<D, P, L>())) return e;
   if ((e = fork_aux(c, 2))) return e;
   if ((ng = lines_groups(S, 0, NW)) > 0) {
-    // one factor slot per block
-    if ((size_t)ng * NW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
-    lines::k_lines_blk<D, P><<<ng, NT, smb, c->st>>>(S);
+    // one factor slot per warp
+    if ((size_t)ng * SH::NWW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
+    lines::k_lines_blk<D, P, L><<<ng, NT, smb, c->st>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 1, NW)) > 0) {
-    lines::k_lines_sca<D, P, 1><<<ng, NT, sms, c->aux[0]>>>(S);
+    lines::k_lines_sca<D, P, L, 1><<<ng, NT, sms, c->aux[0]>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 2, NW)) > 0) {
-    lines::k_lines_sca<D, P, 2><<<ng, NT, sms, c->aux[1]>>>(S);
+    lines::k_lines_sca<D, P, L, 2><<<ng, NT, sms, c->aux[1]>>>(S);
     c->launches++;
   }
   if ((e = join_aux(c, 2))) return e;
@@ -1431,7 +1487,11 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
 
 template <int D>
 static int lines_attr_d(int n) {
-  return n == 64 ? lines_attr<D, 2>() : n == 128 ? lines_attr<D, 4>() : n == 256 ? lines_attr<D, 8>() : SPH_OK;
+  int e = SPH_OK;
+  if (n == 64 && !(e = lines_attr<D, 2, 32>())) e = lines_attr<D, 4, 16>();
+  if (n == 128 && !(e = lines_attr<D, 4, 32>())) e = lines_attr<D, 8, 16>();
+  if (n == 256) e = lines_attr<D, 8, 32>();
+  return e;
 }
 
 static int lines_prepare(const sph_ctx* c) {
@@ -1442,11 +1502,13 @@ static int lines_prepare(const sph_ctx* c) {
   return e;
 }
 
+// lines of 64 and 128 cells: 16 lanes per line unless one warp per line is asked for
 template <int D>
 static int run_lines_d(sph_ctx* c, SweepArgs<float>& S, int n) {
-  if (n == 64) return run_lines<D, 2>(c, S);
-  if (n == 128) return run_lines<D, 4>(c, S);
-  return run_lines<D, 8>(c, S);
+  const int warp = c->line_solver == SPH_LINES_PARTITIONED_WARP;
+  if (n == 64) return warp ? run_lines<D, 2, 32>(c, S) : run_lines<D, 4, 16>(c, S);
+  if (n == 128) return warp ? run_lines<D, 4, 32>(c, S) : run_lines<D, 8, 16>(c, S);
+  return run_lines<D, 8, 32>(c, S);
 }
 
 template <typename R>
@@ -1458,7 +1520,7 @@ static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> 
   S.rhs = rhs; S.x = x; S.update = update; S.base = base; S.uk = uk;
   S.scr = b.scr; S.acc = c->acc; S.flag = c->flag;
   line_layout(c->d64.g, d, S);
-  if (sizeof(R) == sizeof(float) && c->line_solver == SPH_LINES_PARTITIONED && lines_ok(c, d)) {
+  if (sizeof(R) == sizeof(float) && c->line_solver != SPH_LINES_THOMAS && lines_ok(c, d)) {
     SweepArgs<float>& Sf = *reinterpret_cast<SweepArgs<float>*>(&S);
     const Geo<double>& g = c->d64.g;
     int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;

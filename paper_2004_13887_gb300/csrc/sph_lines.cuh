@@ -3,9 +3,10 @@
 // The sweeps solve (I + tau/2 D_d(Ubar)) x = rhs on every line along d (eqs.
 // spl1-spl3): 3x3-block tridiagonal systems for (p, T, u_d) and scalar
 // tridiagonal systems for the two transverse velocity components; periodic phi
-// makes the phi lines cyclic.  Here a line of n = 32 P cells (P = 1, 2, 4, 8)
-// is solved by one warp: lane l owns the cells [l P, l P + P), and its last
-// cell s_l = l P + P - 1 is a separator.
+// makes the phi lines cyclic.  Here a line of n = L P cells is solved by a
+// segment of L lanes of a warp (L = 32, or 16 with two lines per warp; P = 2,
+// 4, 8): lane l owns the cells [l P, l P + P), and its last cell
+// s_l = l P + P - 1 is a separator.
 //
 //  1. Each lane eliminates its interior cells t = 0..P-2 downwards, treating
 //     the separator before its chunk (s_{l-1}, lane l-1's) as a parameter:
@@ -14,10 +15,12 @@
 //     first interior cell through the two separators around the chunk:
 //         x_0 = p_0 + Q_0 X_l + W_0 X_{l-1}.
 //  2. Separator row l, with x_{s-1} from its own chunk and x_{s+1} from lane
-//     l+1's (p_0, Q_0, W_0), couples only X_{l-1}, X_l, X_{l+1}: a 32-row block
+//     l+1's (p_0, Q_0, W_0), couples only X_{l-1}, X_l, X_{l+1}: an L-row block
 //     tridiagonal system (cyclic when the line is), solved by parallel cyclic
 //     reduction with warp shuffles, on rows scaled to an identity diagonal:
-//     steps at lane strides 1, 2, 4, 8, then a 2x2 elimination with lane ^ 16.
+//     steps at lane strides 1, 2, .., L/4, then a 2x2 elimination with lane
+//     l ^ L/2.  Fewer lanes per line mean longer chunks and one reduction step
+//     less: less reduction work per cell.
 //  3. Each lane back-substitutes its interior with X_l and X_{l-1}.
 //
 // This is block Gaussian elimination in a permuted order (the separators
@@ -26,11 +29,11 @@
 // keep, so no pivoting between blocks is needed -- the same assumption as the
 // sequential block Thomas algorithm.
 //
-// A thread block holds NW = 32/P lines.  Their inputs are staged in shared
+// A thread block holds NW = 1024/n lines.  Their inputs are staged in shared
 // memory with coalesced loads (the lines of one block are adjacent in phi for
 // the r- and theta-sweeps, so 4 or 8 lines share each 32-byte sector; a phi
 // line is contiguous), and the increments leave the same way.  The (E, g, H)
-// factors of a block line live in the block's slot of a scratch buffer; they
+// factors of a warp's lines live in the warp's slot of a scratch buffer; they
 // are read back within microseconds, so they are served by L2, and once the
 // back substitution is done the slot's cache lines are discarded from L2
 // (discard.global.L2) so that the dead factors are never written to DRAM.
@@ -49,19 +52,30 @@ constexpr unsigned FULL = 0xffffffffu;
 // per-lane floats of a block-line factor slot: (E, g, H) per interior cell
 __host__ __device__ constexpr int slot_floats(int P) { return (P > 1 ? P - 1 : 1) * NFAC; }
 
-// position in shared memory of cell c (of chunk length P) on line w
-template <int P>
+// Shape of a launch: lines of n = L P cells, L lanes per line (32, or 16 so
+// that a warp holds two lines), P cells per lane; a block holds NW lines and
+// 1024 of their cells (NT = 1024 / P threads, NWW warps).
+template <int P, int L>
+struct Shape {
+  static constexpr int n = L * P, NW = 1024 / n, NT = 1024 / P, NWW = NT / 32, LPW = 32 / L;
+};
+
+// position in shared memory of cell c on block line w: the chunk of lane l of
+// the warp holding the line is one padded row, so that the lanes of a warp
+// reading one cell each of their chunks hit 32 distinct banks
+template <int P, int L>
 __device__ __forceinline__ int sidx(int w, int c) {
-  return (c / P) * LS + (c % P) * (32 / P) + w;
+  using S = Shape<P, L>;
+  return ((w % S::LPW) * L + c / P) * LS + (c % P) * S::NWW + w / S::LPW;
 }
 
 // element e of a block's staging pass -> (line w, cell c): lines adjacent in
 // memory (r, theta sweeps) put w fastest; contiguous lines (phi) put c fastest
-template <int D, int P>
+template <int D, int P, int L>
 __device__ __forceinline__ void elem(int e, int& w, int& c) {
-  constexpr int NW = 32 / P;
-  if (D == 2) { c = e % (32 * P); w = e / (32 * P); }
-  else { w = e % NW; c = e / NW; }
+  using S = Shape<P, L>;
+  if (D == 2) { c = e % S::n; w = e / S::n; }
+  else { w = e % S::NW; c = e / S::NW; }
 }
 
 __device__ __forceinline__ void mm3(const float* X, const float* Y, float* Z) {
@@ -115,11 +129,12 @@ __device__ __forceinline__ void mm3_XC(const float* X, const float* C, float* Z)
   }
 }
 
-template <int NS>
+// o = s of lane src of this lane's segment of L lanes (zero when `zero`)
+template <int NS, int L = 32>
 __device__ __forceinline__ void shfl_get(const float* s, float* o, int src, bool zero) {
 #pragma unroll
   for (int q = 0; q < NS; q++) {
-    float v = __shfl_sync(FULL, s[q], src);
+    float v = __shfl_sync(FULL, s[q], src, L);
     o[q] = zero ? 0.f : v;
   }
 }
@@ -134,20 +149,22 @@ __device__ __forceinline__ void normalise3(const float* A, const float* B, const
   mv3(Bi, r, X + 18);
 }
 
-// Parallel cyclic reduction of the 32-row reduced block system, one row per
-// lane, normalised (A x_{l-s} + x_l + C x_{l+s} = r).  A step with stride s
-// eliminates x_{l-s} and x_{l+s} with the rows of lanes l -+ s:
+// Parallel cyclic reduction of the L-row reduced block system (L = 32 or 16),
+// one row per lane of the line's segment, normalised (A x_{l-s} + x_l +
+// C x_{l+s} = r).  A step with stride s eliminates x_{l-s} and x_{l+s} with
+// the rows of lanes l -+ s:
 //   B = I - A C_lo - C A_up,  A' = -A A_lo,  C' = -C C_up,
 //   r' = r - A r_lo - C r_up,
 // then renormalises; a missing neighbour (end of a non-cyclic line) is a zero
-// row.  After strides 1, 2, 4, 8 every row couples only to the row of lane ^ 16
-// (both sides of a cyclic line meet there; on a non-cyclic line one of A, C is
-// zero):  x + M x_p = r,  x_p + M_p x = r_p  =>  (I - M M_p) x = r - M r_p.
+// row.  After strides 1, 2, .., L/4 every row couples only to the row of lane
+// l ^ L/2 (both sides of a cyclic line meet there; on a non-cyclic line one of
+// A, C is zero):  x + M x_p = r,  x_p + M_p x = r_p  =>  (I - M M_p) x = r - M r_p.
+template <int L>
 __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int* bad) {
 #pragma unroll 1
-  for (int s = 1; s < 16; s <<= 1) {
+  for (int s = 1; s < L / 2; s <<= 1) {
     float o[NR3], A[9], B[9], C[9], r[3], t[9], u[3];
-    shfl_get<NR3>(X, o, (lane - s) & 31, !cyc && lane < s);
+    shfl_get<NR3, L>(X, o, (lane - s) & (L - 1), !cyc && lane < s);
     mm3(X, o + 9, t);
 #pragma unroll
     for (int q = 0; q < 9; q++) B[q] = (q % 4 == 0 ? 1.f : 0.f) - t[q];
@@ -157,7 +174,7 @@ __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int*
     mv3(X, o + 18, u);
 #pragma unroll
     for (int q = 0; q < 3; q++) r[q] = X[18 + q] - u[q];
-    shfl_get<NR3>(X, o, (lane + s) & 31, !cyc && lane + s > 31);
+    shfl_get<NR3, L>(X, o, (lane + s) & (L - 1), !cyc && lane + s > L - 1);
     mm3(X + 9, o, t);
 #pragma unroll
     for (int q = 0; q < 9; q++) B[q] -= t[q];
@@ -174,7 +191,7 @@ __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int*
   for (int z = 0; z < 9; z++) M[z] = X[z] + X[9 + z];
 #pragma unroll
   for (int z = 0; z < 3; z++) M[9 + z] = X[18 + z];
-  shfl_get<12>(M, ph, lane ^ 16, false);
+  shfl_get<12, L>(M, ph, lane ^ (L / 2), false);
   float Sm[9], Si[9], rr[3], u[3];
   mm3(M, ph, Sm);
 #pragma unroll
@@ -187,15 +204,17 @@ __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int*
 }
 
 // The same for the scalar reduced system (a x_{l-s} + x_l + c x_{l+s} = r).
+template <int L>
 __device__ __forceinline__ float pcr1(float a, float c, float r, int lane, int cyc, int* bad) {
 #pragma unroll 1
-  for (int s = 1; s < 16; s <<= 1) {
-    float la = __shfl_sync(FULL, a, (lane - s) & 31), lc = __shfl_sync(FULL, c, (lane - s) & 31);
-    float lr = __shfl_sync(FULL, r, (lane - s) & 31);
-    float ua = __shfl_sync(FULL, a, (lane + s) & 31), uc = __shfl_sync(FULL, c, (lane + s) & 31);
-    float ur = __shfl_sync(FULL, r, (lane + s) & 31);
+  for (int s = 1; s < L / 2; s <<= 1) {
+    int lo = (lane - s) & (L - 1), up = (lane + s) & (L - 1);
+    float la = __shfl_sync(FULL, a, lo, L), lc = __shfl_sync(FULL, c, lo, L);
+    float lr = __shfl_sync(FULL, r, lo, L);
+    float ua = __shfl_sync(FULL, a, up, L), uc = __shfl_sync(FULL, c, up, L);
+    float ur = __shfl_sync(FULL, r, up, L);
     if (!cyc && lane < s) la = lc = lr = 0.f;
-    if (!cyc && lane + s > 31) ua = uc = ur = 0.f;
+    if (!cyc && lane + s > L - 1) ua = uc = ur = 0.f;
     float b = 1.f - a * lc - c * ua;
     if (b == 0.f || !isfinite(b)) *bad |= FLAG_SINGULAR;
     float ib = sdiv(1.f, b);
@@ -204,7 +223,7 @@ __device__ __forceinline__ float pcr1(float a, float c, float r, int lane, int c
     a = an; c = cn;
   }
   float M = a + c;
-  float Mp = __shfl_sync(FULL, M, lane ^ 16), rp = __shfl_sync(FULL, r, lane ^ 16);
+  float Mp = __shfl_sync(FULL, M, lane ^ (L / 2), L), rp = __shfl_sync(FULL, r, lane ^ (L / 2), L);
   float den = 1.f - M * Mp;
   if (den == 0.f || !isfinite(den)) *bad |= FLAG_SINGULAR;
   return sdiv(r - M * rp, den);
@@ -293,42 +312,45 @@ __device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, float* ss
 // ------------------------------------------------------------------ kernels
 // ------------------------------------------------------------------ kernels
 
-// Block lines (p, T, u_D) of direction D, n = 32 P cells per line.
-template <int D, int P>
+// Block lines (p, T, u_D) of direction D, n = L P cells per line, L lanes per line.
+template <int D, int P, int L>
 __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines_blk(SweepArgs<float> S) {
-  constexpr int NW = 32 / P;
-  constexpr int NT = 32 * NW;
+  using SH = Shape<P, L>;
+  constexpr int NW = SH::NW, NT = SH::NT;
   extern __shared__ float sm[];
   const Geo<float>& g = S.g;
-  const int n = 32 * P, cyc = (D == 2 && g.per);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = SH::n, cyc = (D == 2 && g.per);
+  const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;  // warp, lane of the warp
+  const int w = wid * SH::LPW + wl / L, lane = wl % L;      // block line, lane of the line
   const float h = S.h;
   float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
-  float* slot = S.scr + ((size_t)blockIdx.x * NW + w) * (32 * slot_floats(P));
+  float* slot = S.scr + ((size_t)blockIdx.x * SH::NWW + wid) * (32 * slot_floats(P));
   Group G = group_of(S, 0, blockIdx.x, NW);
-  // 1. stage (n NW = P NT elements: P per thread, all copies in flight)
+  // 1. stage (n NW = P NT elements: P per thread, all copies in flight).  The
+  // block lines past the group's last repeat it, so that every lane of a warp
+  // solves a well-posed line; their results are not written back.
 #pragma unroll
   for (int q = 0; q < P; q++) {
     int lw, c;
-    elem<D, P>(threadIdx.x + q * NT, lw, c);
-    if (lw < G.nvalid) stage_block<D>(S, sm, sidx<P>(lw, c), G.a, G.bb + lw, c, n, cyc);
+    elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+    stage_block<D>(S, sm, sidx<P, L>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c, n, cyc);
   }
   cpa_wait_all();
   __syncthreads();
-  if (w < G.nvalid) {
+  {
     // 2. chunk elimination; the slot holds (E, g, H) of each interior cell, lane-interleaved
     float E[9], gg[3], H[9];
     float Xs[NR3];  // the separator row: lower (0-8), C (9-17), r (18-20); diagonal in Bs
     float Bs[9];
-    int a = G.a, b = G.bb + w;
+    int a = G.a, b = G.bb + min(w, G.nvalid - 1);
     // the cell before the chunk's first: Ubar's u_D on the chunk's first face
     // (the wall value at the start of a walled line)
     float uf;
     {
       int m0 = lane * P;
       if (m0 > 0 || cyc) {
-        uf = sm[7 * FS + sidx<P>(w, m0 > 0 ? m0 - 1 : n - 1)];
+        uf = sm[7 * FS + sidx<P, L>(w, m0 > 0 ? m0 - 1 : n - 1)];
       } else {
         int i, j, k;
         line_pos(D, a, b, 0, i, j, k);
@@ -337,14 +359,14 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     }
     Thermo<float> th;
     {
-      int i, j, k, m0 = lane * P, s0 = sidx<P>(w, m0);
+      int i, j, k, m0 = lane * P, s0 = sidx<P, L>(w, m0);
       line_pos(D, a, b, m0, i, j, k);
       th = thermo(g, S.P, i, sm[s0], sm[FS + s0]);
     }
 #pragma unroll 1
     for (int t = 0; t < P; t++) {
       int m = lane * P + t;
-      int si = sidx<P>(w, m);
+      int si = sidx<P, L>(w, m);
       int i, j, k, fi, fj, fk;
       line_pos(D, a, b, m, i, j, k);
       next_face(D, n, m, i, j, k, fi, fj, fk);
@@ -358,7 +380,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       FPt<float> fq = {th.rho, 1.f, ufn};
       if (m < n - 1 || cyc) {
         // the next cell along the line: its thermodynamics serve this face row and the next step
-        int mn = m + 1 == n ? 0 : m + 1, sn = sidx<P>(w, mn);
+        int mn = m + 1 == n ? 0 : m + 1, sn = sidx<P, L>(w, mn);
         int in_, jn, kn;
         line_pos(D, a, b, mn, in_, jn, kn);
         th = thermo(g, S.P, in_, sm[sn], sm[FS + sn]);
@@ -391,7 +413,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
         mm3_XC(Si, C, E);
         mv3(Si, rv, gg);
         mm3(Si, Hs, H);
-        float* s = slot + t * NFAC * 32 + lane;
+        float* s = slot + t * NFAC * 32 + wl;
 #pragma unroll
         for (int q = 0; q < 9; q++) s[q * 32] = E[q];
 #pragma unroll
@@ -426,7 +448,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       for (int q = 0; q < 9; q++) { Q[q] = -E[q]; W[q] = -H[q]; }
 #pragma unroll 1
       for (int t = P - 3; t >= 0; t--) {
-        const float* s = slot + t * NFAC * 32 + lane;
+        const float* s = slot + t * NFAC * 32 + wl;
         float Et[9], gt[3], Ht[9], T9[9], u[3];
 #pragma unroll
         for (int q = 0; q < 9; q++) Et[q] = s[q * 32];
@@ -446,10 +468,10 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       }
       // separator row: x_{s+1} = p' + Q' X_{l+1} + W' X_l from lane l+1
       float pn[3], Qn[9], Wn[9], T9[9], u[3];
-      bool none = !cyc && lane == 31;
-      shfl_get<3>(p, pn, (lane + 1) & 31, none);
-      shfl_get<9>(Q, Qn, (lane + 1) & 31, none);
-      shfl_get<9>(W, Wn, (lane + 1) & 31, none);
+      bool none = !cyc && lane == L - 1;
+      shfl_get<3, L>(p, pn, (lane + 1) & (L - 1), none);
+      shfl_get<9, L>(Q, Qn, (lane + 1) & (L - 1), none);
+      shfl_get<9, L>(W, Wn, (lane + 1) & (L - 1), none);
       mm3_C(Xs + 9, Wn, T9);
 #pragma unroll
       for (int q = 0; q < 9; q++) Bs[q] += T9[q];
@@ -468,17 +490,17 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     }
     // 3. reduced system
     float xs[3], xp[3];
-    pcr3(Xs, lane, cyc, xs, &bad);
-    shfl_get<3>(xs, xp, (lane + 31) & 31, !cyc && lane == 0);
+    pcr3<L>(Xs, lane, cyc, xs, &bad);
+    shfl_get<3, L>(xs, xp, (lane + L - 1) & (L - 1), !cyc && lane == 0);
     // 4. back substitution; each lane writes its increments over its own
     // staged inputs (fields 0-2), which only it reads
-    int sl = sidx<P>(w, lane * P + P - 1);
+    int sl = sidx<P, L>(w, lane * P + P - 1);
 #pragma unroll
     for (int q = 0; q < 3; q++) sm[q * FS + sl] = xs[q];
     float xn[3] = {xs[0], xs[1], xs[2]};
 #pragma unroll 1
     for (int t = P - 2; t >= 0; t--) {
-      const float* s = slot + t * NFAC * 32 + lane;
+      const float* s = slot + t * NFAC * 32 + wl;
       float Et[9], gt[3], Ht[9], u[3], v[3];
 #pragma unroll
       for (int q = 0; q < 9; q++) Et[q] = s[q * 32];
@@ -488,7 +510,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       for (int q = 0; q < 9; q++) Ht[q] = s[(12 + q) * 32];
       mv3(Et, xn, u);
       mv3(Ht, xp, v);
-      int st = sidx<P>(w, lane * P + t);
+      int st = sidx<P, L>(w, lane * P + t);
 #pragma unroll
       for (int q = 0; q < 3; q++) {
         xn[q] = gt[q] - u[q] - v[q];
@@ -498,7 +520,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     if (P > 1) {
       // the slot is dead: drop its lines from L2 without writing them back
       __syncwarp();
-      for (int q = lane; q < slot_floats(P); q += 32)
+      for (int q = wl; q < slot_floats(P); q += 32)
         asm volatile("discard.global.L2 [%0], 128;" ::"l"(slot + q * 32) : "memory");
     }
   }
@@ -511,9 +533,9 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
       if (lw >= G.nvalid) continue;
-      int si = sidx<P>(lw, c);
+      int si = sidx<P, L>(lw, c);
       int i, j, k;
       line_pos(D, G.a, G.bb + lw, c, i, j, k);
       int ic = IC(g, i, j, k);
@@ -534,7 +556,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
       ic[q] = iu[q] = iw[q] = -1;
       if (lw >= G.nvalid) continue;
       int i, j, k;
@@ -557,8 +579,8 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     for (int q = 0; q < P; q++) {
       if (ic[q] < 0) continue;
       int lw, c;
-      elem<D, P>(threadIdx.x + q * NT, lw, c);
-      int si = sidx<P>(lw, c);
+      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+      int si = sidx<P, L>(lw, c);
       put_upd(S, 0, ic[q], bp[q], sm[si], ss, &bad);
       put_upd(S, 4, ic[q], bT[q], sm[FS + si], ss, &bad);
       if (c < n - 1 || cyc) put_upd(S, 1 + D, iu[q], bu[q], sm[2 * FS + si], ss, &bad);
@@ -569,17 +591,17 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
   flush_norms(S, ss, bad);
 }
 
-// Scalar lines of the transverse component trans_comp(D, KIND), n = 32 P.
-template <int D, int P, int KIND>
+// Scalar lines of the transverse component trans_comp(D, KIND), n = L P.
+template <int D, int P, int L, int KIND>
 __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
-  constexpr int NW = 32 / P;
-  constexpr int NT = 32 * NW;
+  using SH = Shape<P, L>;
+  constexpr int NW = SH::NW, NT = SH::NT;
   constexpr int NI = P > 1 ? P - 1 : 1;
   constexpr int cc = trans_comp(D, KIND);
   extern __shared__ float sm[];
   const Geo<float>& g = S.g;
-  const int n = 32 * P, cyc = (D == 2 && g.per);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = SH::n, cyc = (D == 2 && g.per);
+  const int w = (threadIdx.x >> 5) * SH::LPW + (threadIdx.x & 31) / L, lane = (threadIdx.x & 31) % L;
   const float h = S.h;
   float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
@@ -587,19 +609,19 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
 #pragma unroll
   for (int q = 0; q < P; q++) {
     int lw, c;
-    elem<D, P>(threadIdx.x + q * NT, lw, c);
-    if (lw < G.nvalid) stage_scalar<D, KIND>(S, sm, sidx<P>(lw, c), G.a, G.bb + lw, c);
+    elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+    stage_scalar<D, KIND>(S, sm, sidx<P, L>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c);  // see k_lines_blk
   }
   __syncthreads();
-  if (w < G.nvalid) {
-    int a = G.a, b = G.bb + w;
+  {
+    int a = G.a, b = G.bb + min(w, G.nvalid - 1);
     float e_[NI], g_[NI], h_[NI];
     float ep = 0.f, gp = 0.f, hp_ = 0.f;
     float sa = 0.f, sb = 1.f, sc = 0.f, sr = 0.f;  // separator row
 #pragma unroll
     for (int t = 0; t < P; t++) {
       int m = lane * P + t;
-      int si = sidx<P>(w, m);
+      int si = sidx<P, L>(w, m);
       SPt<float> q = {sm[si], sm[FS + si], sm[2 * FS + si]};
       float r = sm[3 * FS + si];
       int i, j, k;
@@ -633,9 +655,10 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
         Q = -e_[t] * Q;
         W = -h_[t] - e_[t] * W;
       }
-      bool none = !cyc && lane == 31;
-      float pn = __shfl_sync(FULL, p, (lane + 1) & 31), Qn = __shfl_sync(FULL, Q, (lane + 1) & 31);
-      float Wn = __shfl_sync(FULL, W, (lane + 1) & 31);
+      bool none = !cyc && lane == L - 1;
+      int up = (lane + 1) & (L - 1);
+      float pn = __shfl_sync(FULL, p, up, L), Qn = __shfl_sync(FULL, Q, up, L);
+      float Wn = __shfl_sync(FULL, W, up, L);
       if (none) pn = Qn = Wn = 0.f;
       sb += sc * Wn;
       sr -= sc * pn;
@@ -643,26 +666,26 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
     }
     if (sb == 0.f || !isfinite(sb)) bad |= FLAG_SINGULAR;
     float ib = sdiv(1.f, sb);
-    float xs = pcr1(sa * ib, sc * ib, sr * ib, lane, cyc, &bad);
-    float xp = __shfl_sync(FULL, xs, (lane + 31) & 31);
+    float xs = pcr1<L>(sa * ib, sc * ib, sr * ib, lane, cyc, &bad);
+    float xp = __shfl_sync(FULL, xs, (lane + L - 1) & (L - 1), L);
     if (!cyc && lane == 0) xp = 0.f;
     float xo[P];
     xo[P - 1] = xs;
 #pragma unroll
     for (int t = P - 2; t >= 0; t--) xo[t] = g_[t] - e_[t] * xo[t + 1] - h_[t] * xp;
 #pragma unroll
-    for (int t = 0; t < P; t++) sm[sidx<P>(w, lane * P + t)] = xo[t];
+    for (int t = 0; t < P; t++) sm[sidx<P, L>(w, lane * P + t)] = xo[t];
   }
   __syncthreads();
   if (!S.update) {
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
       if (lw >= G.nvalid) continue;
       int i, j, k;
       line_pos(D, G.a, G.bb + lw, c, i, j, k);
-      scalar_put(S, cc, i, j, k, sm[sidx<P>(lw, c)], ss, &bad);
+      scalar_put(S, cc, i, j, k, sm[sidx<P, L>(lw, c)], ss, &bad);
     }
   } else {
     // every FP64 state value first, then the stores (see the block-line kernel)
@@ -671,7 +694,7 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
       iv[q] = -1;
       if (lw >= G.nvalid) continue;
       int i, j, k;
@@ -683,8 +706,8 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
     for (int q = 0; q < P; q++) {
       if (iv[q] < 0) continue;
       int lw, c;
-      elem<D, P>(threadIdx.x + q * NT, lw, c);
-      put_upd(S, 1 + cc, iv[q], bv[q], sm[sidx<P>(lw, c)], ss, &bad);
+      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+      put_upd(S, 1 + cc, iv[q], bv[q], sm[sidx<P, L>(lw, c)], ss, &bad);
       int i, j, k;
       line_pos(D, G.a, G.bb + lw, c, i, j, k);
       scalar_walls(S, cc, i, j, k);

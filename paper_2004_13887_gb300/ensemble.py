@@ -5,7 +5,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import SPH_LINES_PARTITIONED, SPH_LINES_THOMAS, SPH_PREC_MIXED, Batch, Solver
+from . import SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS, SPH_PREC_MIXED, Batch, Solver
 
 
 def _partitioned_applies(grid) -> bool:
@@ -40,7 +40,7 @@ def autotune(cases, dt, n_iter):
             choice[shape] = SPH_LINES_THOMAS
             continue
         best, best_ms = None, None
-        for which in (SPH_LINES_PARTITIONED, SPH_LINES_THOMAS):
+        for which in (SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS):
             s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
             s.set_background(*c.bg)
             s.set_state([torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init])

@@ -104,10 +104,11 @@ def test_autotune_choices_agree():
     cs = _cases()
     choice = ensemble.autotune(cs, 1.0, 2)
     assert set(choice) == {(c.grid.nr, c.grid.nt, c.grid.np) for c in cs}
-    assert all(v in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED) for v in choice.values())
+    assert all(v in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP)
+               for v in choice.values())
     c = cs[5]   # 64 x 64 x 128: both solvers apply
     xs = []
-    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED):
+    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP):
         s = _solver(c)
         s.set_line_solver(which)
         for _ in range(2):
@@ -116,7 +117,8 @@ def test_autotune_choices_agree():
         s.close()
     for f in range(5):
         scale = float(np.max(np.abs(xs[0][f] - c.init[f]))) or 1.0
-        assert float(np.max(np.abs(xs[0][f] - xs[1][f]))) <= 1e-5 * scale
+        for x in xs[1:]:
+            assert float(np.max(np.abs(xs[0][f] - x[f]))) <= 1e-5 * scale
 
 
 def test_ensemble_of_config_five():

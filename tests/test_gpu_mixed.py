@@ -125,14 +125,20 @@ def test_mixed_steps_full_size_bubble():
         assert v <= 1e-6, (k, v)
 
 
-# Line lengths 64, 128, 256 in every direction (chunks of 2, 4, 8 cells per
-# lane), periodic and walled phi, a pole, and a direction of another length
-# (40: block Thomas) next to partitioned ones.
+# Line lengths 64, 128, 256 in every direction (16 lanes per line with chunks
+# of 4 and 8 cells, 32 lanes with chunks of 8), periodic and walled phi, a
+# pole, directions of other lengths (block Thomas) next to partitioned ones,
+# and line counts that leave the last group of a launch partly empty (r lines
+# of 64 and 128 cells in groups of 16 and 8; cyclic phi lines of 128 in groups
+# of 8).
 PART_CASES = {
     "bubble_64x64x128": lambda: _bubble((64, 64, 128)),
     "shell_64x128x256": lambda: _shell((64, 128, 256), pole=False),
     "shell_pole_128x64x64": lambda: _shell((128, 64, 64), pole=True),
     "sector_40x256x64": lambda: _sector((40, 256, 64)),
+    "sector_64x36x100": lambda: _sector((64, 36, 100)),
+    "bubble_128x24x20": lambda: _bubble((128, 24, 20)),
+    "shell_40x36x128": lambda: _shell((40, 36, 128), pole=False),
 }
 
 
@@ -158,11 +164,14 @@ def test_line_solver_option():
     rhs = to_dev(perturbed(g.zeros(), [1.0] * 5, 40, g))
     for d in range(3):
         xp = to_host(s.sweep(d, dt, rhs))
+        s.set_line_solver(sph.SPH_LINES_PARTITIONED_WARP)
+        xw = to_host(s.sweep(d, dt, rhs))
         s.set_line_solver(sph.SPH_LINES_THOMAS)
         xt = to_host(s.sweep(d, dt, rhs))
         s.set_line_solver(sph.SPH_LINES_PARTITIONED)
         for q in range(5):
             assert rel_err(xp[q], xt[q]) <= 1e-5, (d, q, rel_err(xp[q], xt[q]))
+            assert rel_err(xw[q], xt[q]) <= 1e-5, (d, q, rel_err(xw[q], xt[q]))
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
@@ -186,7 +195,8 @@ def test_partitioned_steps_cyclic():
     """Whole steps on a periodic shell: partitioned vs Thomas vs FP64."""
     g, par, bg, Un, Uk, S, dt = PART_CASES["shell_64x128x256"]()
     outs = []
-    for prec, which in ((sph.SPH_PREC_FP64, None), (MIXED, sph.SPH_LINES_THOMAS), (MIXED, sph.SPH_LINES_PARTITIONED)):
+    for prec, which in ((sph.SPH_PREC_FP64, None), (MIXED, sph.SPH_LINES_THOMAS), (MIXED, sph.SPH_LINES_PARTITIONED),
+                        (MIXED, sph.SPH_LINES_PARTITIONED_WARP)):
         s = solver_for(g, par, bg, Un, precision=prec)
         if which is not None:
             s.set_line_solver(which)
