@@ -1404,21 +1404,30 @@ static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
 }
 
 // Partitioned line solver (mixed path) for lines of n = L P cells, L lanes
-// per line: one launch per line kind, one block per group of 1024/n lines.
-// The shared-memory size attribute of the block-line kernel of a (D, P, L),
-// set once per process (at context creation, so that no attribute call falls
+// per line: one launch per line kind, one block per group of CB/n lines.
+// The shared-memory size attributes of the kernels of a (D, P, L, CB), set
+// once per process (at context creation, so that no attribute call falls
 // inside a CUDA graph capture).
-template <int D, int P, int L>
+template <int D, int P, int L, int CB>
 static int lines_attr() {
   static int done = 0;
   if (done) return SPH_OK;
-  const int smb = lines::NFB * lines::FS * (int)sizeof(float);
-  if (cudaFuncSetAttribute(lines::k_lines_blk<D, P, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) !=
-      cudaSuccess)
+  const int smb = lines::NFB * lines::Shape<P, L, CB>::FS * (int)sizeof(float);
+  const int sms = lines::NFS * lines::Shape<P, L, CB>::FS * (int)sizeof(float);
+  if (cudaFuncSetAttribute(lines::k_lines_blk<D, P, L, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(lines::k_lines_sca<D, P, L, CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(lines::k_lines_sca<D, P, L, CB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms) !=
+          cudaSuccess)
     return SPH_ERR_CUDA;
   done = 1;
   return SPH_OK;
 }
+
+// cells per block of the partitioned solver: 2048 for 256-cell lines along r
+// and theta (8 adjacent lines per block fill each 32-byte sector), else 1024
+__host__ __device__ constexpr int lines_cb(int D, int n) { return D != 2 && n == 256 ? 2048 : 1024; }
 
 static int lines_groups(const SweepArgs<float>& S, int kind, int NW) {
   if (S.nl[kind] <= 0) return 0;
@@ -1441,7 +1450,7 @@ static size_t lines_scratch(int nr, int nt, int np, int per) {
     line_layout(g, d, S);
     for (int L = 16; L <= 32; L += 16) {
       if (L == 16 && n == 256) continue;
-      int P = n / L, NW = 1024 / n, NWW = 1024 / P / 32;
+      int P = n / L, CB = lines_cb(d, n), NW = CB / n, NWW = CB / P / 32;
       size_t need = (size_t)lines_groups(S, 0, NW) * NWW * 32 * lines::slot_floats(P);
       if (need > mx) mx = need;
     }
@@ -1458,26 +1467,27 @@ static int lines_ok(const sph_ctx* c, int d) {
 
 template <int D, int P, int L>
 static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
-  using SH = lines::Shape<P, L>;
+  constexpr int CB = lines_cb(D, L * P);
+  using SH = lines::Shape<P, L, CB>;
   constexpr int NW = SH::NW, NT = SH::NT;
-  const size_t smb = (size_t)lines::NFB * lines::FS * sizeof(float);
-  const size_t sms = (size_t)lines::NFS * lines::FS * sizeof(float);
+  const size_t smb = (size_t)lines::NFB * SH::FS * sizeof(float);
+  const size_t sms = (size_t)lines::NFS * SH::FS * sizeof(float);
   int ng, e;
   k_begin(c, SPH_K_SWEEP_R + D);
-  if ((e = lines_attr<D, P, L>())) return e;
+  if ((e = lines_attr<D, P, L, CB>())) return e;
   if ((e = fork_aux(c, 2))) return e;
   if ((ng = lines_groups(S, 0, NW)) > 0) {
     // one factor slot per warp
     if ((size_t)ng * SH::NWW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
-    lines::k_lines_blk<D, P, L><<<ng, NT, smb, c->st>>>(S);
+    lines::k_lines_blk<D, P, L, CB><<<ng, NT, smb, c->st>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 1, NW)) > 0) {
-    lines::k_lines_sca<D, P, L, 1><<<ng, NT, sms, c->aux[0]>>>(S);
+    lines::k_lines_sca<D, P, L, CB, 1><<<ng, NT, sms, c->aux[0]>>>(S);
     c->launches++;
   }
   if ((ng = lines_groups(S, 2, NW)) > 0) {
-    lines::k_lines_sca<D, P, L, 2><<<ng, NT, sms, c->aux[1]>>>(S);
+    lines::k_lines_sca<D, P, L, CB, 2><<<ng, NT, sms, c->aux[1]>>>(S);
     c->launches++;
   }
   if ((e = join_aux(c, 2))) return e;
@@ -1488,9 +1498,9 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
 template <int D>
 static int lines_attr_d(int n) {
   int e = SPH_OK;
-  if (n == 64 && !(e = lines_attr<D, 2, 32>())) e = lines_attr<D, 4, 16>();
-  if (n == 128 && !(e = lines_attr<D, 4, 32>())) e = lines_attr<D, 8, 16>();
-  if (n == 256) e = lines_attr<D, 8, 32>();
+  if (n == 64 && !(e = lines_attr<D, 2, 32, lines_cb(D, 64)>())) e = lines_attr<D, 4, 16, lines_cb(D, 64)>();
+  if (n == 128 && !(e = lines_attr<D, 4, 32, lines_cb(D, 128)>())) e = lines_attr<D, 8, 16, lines_cb(D, 128)>();
+  if (n == 256) e = lines_attr<D, 8, 32, lines_cb(D, 256)>();
   return e;
 }
 

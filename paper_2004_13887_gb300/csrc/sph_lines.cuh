@@ -29,10 +29,11 @@
 // keep, so no pivoting between blocks is needed -- the same assumption as the
 // sequential block Thomas algorithm.
 //
-// A thread block holds NW = 1024/n lines.  Their inputs are staged in shared
-// memory with coalesced loads (the lines of one block are adjacent in phi for
-// the r- and theta-sweeps, so 4 or 8 lines share each 32-byte sector; a phi
-// line is contiguous), and the increments leave the same way.  The (E, g, H)
+// A thread block holds NW = CB/n lines of CB cells.  Their inputs are staged
+// in shared memory with coalesced loads (the lines of one block are adjacent in
+// phi for the r- and theta-sweeps; CB = 2048 for lines of 256 cells there, so
+// that 8 lines fill each 32-byte sector, else 1024; a phi line is contiguous),
+// and the increments leave the same way.  The (E, g, H)
 // factors of a warp's lines live in the warp's slot of a scratch buffer; they
 // are read back within microseconds, so they are served by L2, and once the
 // back substitution is done the slot's cache lines are discarded from L2
@@ -41,8 +42,6 @@
 
 namespace lines {
 
-constexpr int LS = 33;        // shared-memory stride of one lane's chunk: 32 values + 1 pad
-constexpr int FS = 32 * LS;   // shared-memory stride of one staged field
 constexpr int NFB = 11;       // staged fields of a block line
 constexpr int NFS = 4;        // staged fields of a scalar line
 constexpr int NFAC = 21;      // E (9), g (3), H (9) per interior cell
@@ -54,26 +53,29 @@ __host__ __device__ constexpr int slot_floats(int P) { return (P > 1 ? P - 1 : 1
 
 // Shape of a launch: lines of n = L P cells, L lanes per line (32, or 16 so
 // that a warp holds two lines), P cells per lane; a block holds NW lines and
-// 1024 of their cells (NT = 1024 / P threads, NWW warps).
-template <int P, int L>
+// CB of their cells (NT = CB / P threads, NWW warps).  In shared memory each
+// staged field is 32 rows of CB/32 values and one word of padding (LS), FS
+// floats in all.
+template <int P, int L, int CB>
 struct Shape {
-  static constexpr int n = L * P, NW = 1024 / n, NT = 1024 / P, NWW = NT / 32, LPW = 32 / L;
+  static constexpr int n = L * P, NW = CB / n, NT = CB / P, NWW = NT / 32, LPW = 32 / L;
+  static constexpr int LS = CB / 32 + 1, FS = 32 * LS;
 };
 
 // position in shared memory of cell c on block line w: the chunk of lane l of
 // the warp holding the line is one padded row, so that the lanes of a warp
 // reading one cell each of their chunks hit 32 distinct banks
-template <int P, int L>
+template <int P, int L, int CB>
 __device__ __forceinline__ int sidx(int w, int c) {
-  using S = Shape<P, L>;
-  return ((w % S::LPW) * L + c / P) * LS + (c % P) * S::NWW + w / S::LPW;
+  using S = Shape<P, L, CB>;
+  return ((w % S::LPW) * L + c / P) * S::LS + (c % P) * S::NWW + w / S::LPW;
 }
 
 // element e of a block's staging pass -> (line w, cell c): lines adjacent in
 // memory (r, theta sweeps) put w fastest; contiguous lines (phi) put c fastest
-template <int D, int P, int L>
+template <int D, int P, int L, int CB>
 __device__ __forceinline__ void elem(int e, int& w, int& c) {
-  using S = Shape<P, L>;
+  using S = Shape<P, L, CB>;
   if (D == 2) { c = e % S::n; w = e / S::n; }
   else { w = e % S::NW; c = e / S::NW; }
 }
@@ -247,7 +249,7 @@ __device__ __forceinline__ void cpa_wait_all() {
 // velocity-gradient coefficients, Ubar's u_D on face c+1 (the centre velocity
 // is the mean of the cell's two faces) and the three right-hand-side values
 // (the last face of a walled line has no row: zero)
-template <int D>
+template <int D, int FS>
 __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c, int n,
                                             int cyc) {
   const Geo<float>& g = S.g;
@@ -272,7 +274,7 @@ __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm
 // stage the inputs of scalar-line cell c (component cc) of line (a, b); away
 // from the r and theta walls the averaged velocities come from the coefficient
 // planes without checks
-template <int D, int KIND>
+template <int D, int KIND, int FS>
 __device__ __forceinline__ void stage_scalar(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c) {
   const Geo<float>& g = S.g;
   constexpr int cc = trans_comp(D, KIND);
@@ -312,11 +314,12 @@ __device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, float* ss
 // ------------------------------------------------------------------ kernels
 // ------------------------------------------------------------------ kernels
 
-// Block lines (p, T, u_D) of direction D, n = L P cells per line, L lanes per line.
-template <int D, int P, int L>
-__global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines_blk(SweepArgs<float> S) {
-  using SH = Shape<P, L>;
-  constexpr int NW = SH::NW, NT = SH::NT;
+// Block lines (p, T, u_D) of direction D, n = L P cells per line, L lanes per
+// line, CB cells per block (at most 128 registers a thread).
+template <int D, int P, int L, int CB>
+__global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<float> S) {
+  using SH = Shape<P, L, CB>;
+  constexpr int NW = SH::NW, NT = SH::NT, FS = SH::FS;
   extern __shared__ float sm[];
   const Geo<float>& g = S.g;
   const int n = SH::n, cyc = (D == 2 && g.per);
@@ -333,8 +336,8 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
 #pragma unroll
   for (int q = 0; q < P; q++) {
     int lw, c;
-    elem<D, P, L>(threadIdx.x + q * NT, lw, c);
-    stage_block<D>(S, sm, sidx<P, L>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c, n, cyc);
+    elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
+    stage_block<D, FS>(S, sm, sidx<P, L, CB>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c, n, cyc);
   }
   cpa_wait_all();
   __syncthreads();
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     {
       int m0 = lane * P;
       if (m0 > 0 || cyc) {
-        uf = sm[7 * FS + sidx<P, L>(w, m0 > 0 ? m0 - 1 : n - 1)];
+        uf = sm[7 * FS + sidx<P, L, CB>(w, m0 > 0 ? m0 - 1 : n - 1)];
       } else {
         int i, j, k;
         line_pos(D, a, b, 0, i, j, k);
@@ -359,14 +362,14 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     }
     Thermo<float> th;
     {
-      int i, j, k, m0 = lane * P, s0 = sidx<P, L>(w, m0);
+      int i, j, k, m0 = lane * P, s0 = sidx<P, L, CB>(w, m0);
       line_pos(D, a, b, m0, i, j, k);
       th = thermo(g, S.P, i, sm[s0], sm[FS + s0]);
     }
 #pragma unroll 1
     for (int t = 0; t < P; t++) {
       int m = lane * P + t;
-      int si = sidx<P, L>(w, m);
+      int si = sidx<P, L, CB>(w, m);
       int i, j, k, fi, fj, fk;
       line_pos(D, a, b, m, i, j, k);
       next_face(D, n, m, i, j, k, fi, fj, fk);
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       FPt<float> fq = {th.rho, 1.f, ufn};
       if (m < n - 1 || cyc) {
         // the next cell along the line: its thermodynamics serve this face row and the next step
-        int mn = m + 1 == n ? 0 : m + 1, sn = sidx<P, L>(w, mn);
+        int mn = m + 1 == n ? 0 : m + 1, sn = sidx<P, L, CB>(w, mn);
         int in_, jn, kn;
         line_pos(D, a, b, mn, in_, jn, kn);
         th = thermo(g, S.P, in_, sm[sn], sm[FS + sn]);
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     shfl_get<3, L>(xs, xp, (lane + L - 1) & (L - 1), !cyc && lane == 0);
     // 4. back substitution; each lane writes its increments over its own
     // staged inputs (fields 0-2), which only it reads
-    int sl = sidx<P, L>(w, lane * P + P - 1);
+    int sl = sidx<P, L, CB>(w, lane * P + P - 1);
 #pragma unroll
     for (int q = 0; q < 3; q++) sm[q * FS + sl] = xs[q];
     float xn[3] = {xs[0], xs[1], xs[2]};
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
       for (int q = 0; q < 9; q++) Ht[q] = s[(12 + q) * 32];
       mv3(Et, xn, u);
       mv3(Ht, xp, v);
-      int st = sidx<P, L>(w, lane * P + t);
+      int st = sidx<P, L, CB>(w, lane * P + t);
 #pragma unroll
       for (int q = 0; q < 3; q++) {
         xn[q] = gt[q] - u[q] - v[q];
@@ -533,9 +536,9 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
       if (lw >= G.nvalid) continue;
-      int si = sidx<P, L>(lw, c);
+      int si = sidx<P, L, CB>(lw, c);
       int i, j, k;
       line_pos(D, G.a, G.bb + lw, c, i, j, k);
       int ic = IC(g, i, j, k);
@@ -556,7 +559,7 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
       ic[q] = iu[q] = iw[q] = -1;
       if (lw >= G.nvalid) continue;
       int i, j, k;
@@ -579,8 +582,8 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
     for (int q = 0; q < P; q++) {
       if (ic[q] < 0) continue;
       int lw, c;
-      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
-      int si = sidx<P, L>(lw, c);
+      elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
+      int si = sidx<P, L, CB>(lw, c);
       put_upd(S, 0, ic[q], bp[q], sm[si], ss, &bad);
       put_upd(S, 4, ic[q], bT[q], sm[FS + si], ss, &bad);
       if (c < n - 1 || cyc) put_upd(S, 1 + D, iu[q], bu[q], sm[2 * FS + si], ss, &bad);
@@ -591,11 +594,11 @@ __global__ void __launch_bounds__(1024 / P, P == 8 ? 4 : P == 4 ? 2 : 1) k_lines
   flush_norms(S, ss, bad);
 }
 
-// Scalar lines of the transverse component trans_comp(D, KIND), n = L P.
-template <int D, int P, int L, int KIND>
-__global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
-  using SH = Shape<P, L>;
-  constexpr int NW = SH::NW, NT = SH::NT;
+// Scalar lines of the transverse component trans_comp(D, KIND), n = L P, CB cells per block.
+template <int D, int P, int L, int CB, int KIND>
+__global__ void __launch_bounds__(CB / P) k_lines_sca(SweepArgs<float> S) {
+  using SH = Shape<P, L, CB>;
+  constexpr int NW = SH::NW, NT = SH::NT, FS = SH::FS;
   constexpr int NI = P > 1 ? P - 1 : 1;
   constexpr int cc = trans_comp(D, KIND);
   extern __shared__ float sm[];
@@ -609,8 +612,8 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
 #pragma unroll
   for (int q = 0; q < P; q++) {
     int lw, c;
-    elem<D, P, L>(threadIdx.x + q * NT, lw, c);
-    stage_scalar<D, KIND>(S, sm, sidx<P, L>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c);  // see k_lines_blk
+    elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
+    stage_scalar<D, KIND, FS>(S, sm, sidx<P, L, CB>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c);  // see k_lines_blk
   }
   __syncthreads();
   {
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
 #pragma unroll
     for (int t = 0; t < P; t++) {
       int m = lane * P + t;
-      int si = sidx<P, L>(w, m);
+      int si = sidx<P, L, CB>(w, m);
       SPt<float> q = {sm[si], sm[FS + si], sm[2 * FS + si]};
       float r = sm[3 * FS + si];
       int i, j, k;
@@ -674,18 +677,18 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
 #pragma unroll
     for (int t = P - 2; t >= 0; t--) xo[t] = g_[t] - e_[t] * xo[t + 1] - h_[t] * xp;
 #pragma unroll
-    for (int t = 0; t < P; t++) sm[sidx<P, L>(w, lane * P + t)] = xo[t];
+    for (int t = 0; t < P; t++) sm[sidx<P, L, CB>(w, lane * P + t)] = xo[t];
   }
   __syncthreads();
   if (!S.update) {
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
       if (lw >= G.nvalid) continue;
       int i, j, k;
       line_pos(D, G.a, G.bb + lw, c, i, j, k);
-      scalar_put(S, cc, i, j, k, sm[sidx<P, L>(lw, c)], ss, &bad);
+      scalar_put(S, cc, i, j, k, sm[sidx<P, L, CB>(lw, c)], ss, &bad);
     }
   } else {
     // every FP64 state value first, then the stores (see the block-line kernel)
@@ -694,7 +697,7 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
 #pragma unroll
     for (int q = 0; q < P; q++) {
       int lw, c;
-      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
+      elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
       iv[q] = -1;
       if (lw >= G.nvalid) continue;
       int i, j, k;
@@ -706,8 +709,8 @@ __global__ void __launch_bounds__(1024 / P) k_lines_sca(SweepArgs<float> S) {
     for (int q = 0; q < P; q++) {
       if (iv[q] < 0) continue;
       int lw, c;
-      elem<D, P, L>(threadIdx.x + q * NT, lw, c);
-      put_upd(S, 1 + cc, iv[q], bv[q], sm[sidx<P, L>(lw, c)], ss, &bad);
+      elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
+      put_upd(S, 1 + cc, iv[q], bv[q], sm[sidx<P, L, CB>(lw, c)], ss, &bad);
       int i, j, k;
       line_pos(D, G.a, G.bb + lw, c, i, j, k);
       scalar_walls(S, cc, i, j, k);

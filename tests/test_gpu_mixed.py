@@ -129,8 +129,8 @@ def test_mixed_steps_full_size_bubble():
 # of 4 and 8 cells, 32 lanes with chunks of 8), periodic and walled phi, a
 # pole, directions of other lengths (block Thomas) next to partitioned ones,
 # and line counts that leave the last group of a launch partly empty (r lines
-# of 64 and 128 cells in groups of 16 and 8; cyclic phi lines of 128 in groups
-# of 8).
+# of 64, 128 and 256 cells in groups of 16, 8 and 8; theta lines of 256 in
+# groups of 8; cyclic phi lines of 128 in groups of 8).
 PART_CASES = {
     "bubble_64x64x128": lambda: _bubble((64, 64, 128)),
     "shell_64x128x256": lambda: _shell((64, 128, 256), pole=False),
@@ -139,6 +139,8 @@ PART_CASES = {
     "sector_64x36x100": lambda: _sector((64, 36, 100)),
     "bubble_128x24x20": lambda: _bubble((128, 24, 20)),
     "shell_40x36x128": lambda: _shell((40, 36, 128), pole=False),
+    "sector_40x256x20": lambda: _sector((40, 256, 20)),
+    "bubble_256x20x12": lambda: _bubble((256, 20, 12)),
 }
 
 
