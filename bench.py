@@ -53,11 +53,12 @@ HBM_PEAK_GBS = 6780.4     # measured copy bandwidth of the GB300s
 MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rhs": 100, "coef": 76, "avg": 100}
 
 # DRAM traffic of each mixed stage measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over the stage's launches in one Picard iteration, per
-# grid point; profiles/stages_bubble_128x256x256_mixed.md) and the hash of the
-# kernel sources it was measured on: reported only while the sources match.
-MEASURED_TRAFFIC = {"avg": 86.4, "coef": 69.6, "rhs": 192.9, "sweep_r": 74.8, "sweep_theta": 79.3, "sweep_phi": 140.2}
-TRAFFIC_SOURCE_HASH = "fca5444c3c65fd0f"
+# dram__bytes_write.sum over the stage's launches, per grid point, the mean of
+# the two Picard iterations of a step; profiles/stages_bubble_128x256x256_mixed.md)
+# and the hash of the kernel sources it was measured on: reported only while
+# the sources match.
+MEASURED_TRAFFIC = {"avg": 98.2, "coef": 69.2, "rhs": 202.0, "sweep_r": 73.7, "sweep_theta": 78.2, "sweep_phi": 137.3}
+TRAFFIC_SOURCE_HASH = "460714b22ee6188d"
 
 
 def kernel_source_hash():
