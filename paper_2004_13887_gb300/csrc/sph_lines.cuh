@@ -11,9 +11,10 @@
 //  1. Each lane eliminates its interior cells t = 0..P-2 downwards, treating
 //     the separator before its chunk (s_{l-1}, lane l-1's) as a parameter:
 //         x_t = g_t - E_t x_{t+1} - H_t X_{l-1},
-//     storing (E, g, H), and then runs the recursion back up to express its
-//     first interior cell through the two separators around the chunk:
-//         x_0 = p_0 + Q_0 X_l + W_0 X_{l-1}.
+//     storing (E, g, H), and carries along the expression of its first
+//     interior cell through the next unknown, x_0 = p + Q x_{t+1} + W X_{l-1}
+//     (p += Q g_t, W -= Q H_t, Q = -Q E_t), which after the last interior cell
+//     is x_0 = p + Q X_l + W X_{l-1}.
 //  2. Separator row l, with x_{s-1} from its own chunk and x_{s+1} from lane
 //     l+1's (p_0, Q_0, W_0), couples only X_{l-1}, X_l, X_{l+1}: an L-row block
 //     tridiagonal system (cyclic when the line is), solved by parallel cyclic
@@ -346,6 +347,8 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
     float E[9], gg[3], H[9];
     float Xs[NR3];  // the separator row: lower (0-8), C (9-17), r (18-20); diagonal in Bs
     float Bs[9];
+    // x_0 = p + Q x_{t+1} + W X_{l-1}, carried down the chunk with the elimination
+    float p[3], Q[9], W[9];
     int a = G.a, b = G.bb + min(w, G.nvalid - 1);
     // the cell before the chunk's first: Ubar's u_D on the chunk's first face
     // (the wall value at the start of a walled line)
@@ -416,6 +419,25 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
         mm3_XC(Si, C, E);
         mv3(Si, rv, gg);
         mm3(Si, Hs, H);
+        // with x_t = g_t - E_t x_{t+1} - H_t X_{l-1}:
+        //   p <- p + Q g_t,  W <- W - Q H_t,  Q <- -Q E_t
+        if (t == 0) {
+#pragma unroll
+          for (int q = 0; q < 3; q++) p[q] = gg[q];
+#pragma unroll
+          for (int q = 0; q < 9; q++) { Q[q] = -E[q]; W[q] = -H[q]; }
+        } else {
+          float T9[9], u[3];
+          mv3(Q, gg, u);
+#pragma unroll
+          for (int q = 0; q < 3; q++) p[q] += u[q];
+          mm3(Q, H, T9);
+#pragma unroll
+          for (int q = 0; q < 9; q++) W[q] -= T9[q];
+          mm3(Q, E, T9);
+#pragma unroll
+          for (int q = 0; q < 9; q++) Q[q] = -T9[q];
+        }
         float* s = slot + t * NFAC * 32 + wl;
 #pragma unroll
         for (int q = 0; q < 9; q++) s[q * 32] = E[q];
@@ -443,32 +465,7 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
       }
     }
     if (P > 1) {
-      // x_0 = p + Q X_l + W X_{l-1}, from the top of the chunk's recursion
-      float p[3], Q[9], W[9];
-#pragma unroll
-      for (int q = 0; q < 3; q++) p[q] = gg[q];
-#pragma unroll
-      for (int q = 0; q < 9; q++) { Q[q] = -E[q]; W[q] = -H[q]; }
-#pragma unroll 1
-      for (int t = P - 3; t >= 0; t--) {
-        const float* s = slot + t * NFAC * 32 + wl;
-        float Et[9], gt[3], Ht[9], T9[9], u[3];
-#pragma unroll
-        for (int q = 0; q < 9; q++) Et[q] = s[q * 32];
-#pragma unroll
-        for (int q = 0; q < 3; q++) gt[q] = s[(9 + q) * 32];
-#pragma unroll
-        for (int q = 0; q < 9; q++) Ht[q] = s[(12 + q) * 32];
-        mv3(Et, p, u);
-#pragma unroll
-        for (int q = 0; q < 3; q++) p[q] = gt[q] - u[q];
-        mm3(Et, Q, T9);
-#pragma unroll
-        for (int q = 0; q < 9; q++) Q[q] = -T9[q];
-        mm3(Et, W, T9);
-#pragma unroll
-        for (int q = 0; q < 9; q++) W[q] = -Ht[q] - T9[q];
-      }
+      // x_0 = p + Q X_l + W X_{l-1} (the elimination's last interior cell had x_{t+1} = X_l)
       // separator row: x_{s+1} = p' + Q' X_{l+1} + W' X_l from lane l+1
       float pn[3], Qn[9], Wn[9], T9[9], u[3];
       bool none = !cyc && lane == L - 1;
