@@ -313,15 +313,18 @@ def run_ours(args, rank, world, dist):
         p.numpy()[...] = f
     host = [p.numpy() for p in pinned]
     nb = sum(int(np.prod(s)) * 8 for s in solver.shapes)
+    out_pinned = [torch.empty(s, dtype=torch.float64).pin_memory() for s in solver.shapes]
+    out = [p.numpy() for p in out_pinned]
     e2e_steps = max(3, min(args.steps, 10))
     solver.set_state(host)
     solver.step(DT, K_ITER)
+    solver.get_state(device=False, out=out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         solver.set_state(host)
         solver.step(DT, K_ITER)
-        out = solver.get_state(device=False)
+        solver.get_state(device=False, out=out)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = job_throughput(N, e2e_steps, world, e2e_s * 1e3)

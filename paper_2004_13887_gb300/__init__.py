@@ -159,6 +159,11 @@ class _Ptrs:
         self.arr = (_DP * 5)(*ptrs)
 
 
+def torch_float64():
+    import torch
+    return torch.float64
+
+
 class Solver:
     """One sector (or shell) and its state on the current CUDA device.
 
@@ -207,7 +212,20 @@ class Solver:
         import torch
         return [torch.empty(s, dtype=torch.float64, device="cuda") for s in self.shapes]
 
-    def get_state(self, device: bool = True):
+    def get_state(self, device: bool = True, out=None):
+        """The state U^n: new CUDA tensors (device=True) or numpy arrays, or
+        written into `out` (5 CUDA float64 tensors, or 5 C-contiguous float64
+        numpy arrays -- pinned host memory makes the copy fastest)."""
+        if out is not None:
+            dev = not isinstance(out[0], np.ndarray)
+            for f in out:
+                ok = (f.is_contiguous() and f.dtype == torch_float64()) if dev else \
+                    (isinstance(f, np.ndarray) and f.dtype == np.float64 and f.flags["C_CONTIGUOUS"] and f.flags["WRITEABLE"])
+                if not ok:
+                    raise ValueError("out fields must be contiguous, writeable float64 arrays (or CUDA tensors)")
+            p = _Ptrs(out, self.shapes, dev)
+            _check(load().sph_get_state(self._h, p.arr, int(dev)), "sph_get_state")
+            return out
         if device:
             out = self.empty()
             p = _Ptrs(out, self.shapes, True)

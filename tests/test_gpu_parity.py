@@ -175,6 +175,29 @@ def test_nonfinite_state_is_rejected_and_state_kept():
     assert e.value.code == -1
 
 
+def test_get_state_into_caller_buffers():
+    """get_state(out=...) fills pinned host arrays and CUDA tensors with the
+    state get_state() returns, and refuses buffers it could not write in place."""
+    import torch
+    c = cases.bubble((10, 12, 14), seed=2, dt=1.0)
+    s = solver_for(c.grid, c.par, c.bg, c.init, precision=sph.SPH_PREC_MIXED)
+    s.step(c.dt, 2)
+    ref = s.get_state(device=False)
+    pinned = [torch.empty(sh, dtype=torch.float64).pin_memory() for sh in s.shapes]
+    host = [p.numpy() for p in pinned]
+    assert s.get_state(device=False, out=host) is host
+    dev = [torch.empty(sh, dtype=torch.float64, device="cuda") for sh in s.shapes]
+    s.get_state(out=dev)
+    for q in range(5):
+        assert np.array_equal(host[q], ref[q])
+        assert np.array_equal(dev[q].cpu().numpy(), ref[q])
+    strided = [np.empty((sh[0], sh[1], 2 * sh[2]))[:, :, ::2] for sh in s.shapes]
+    with pytest.raises(ValueError):
+        s.get_state(device=False, out=strided)
+    with pytest.raises(ValueError):
+        s.get_state(device=False, out=[h.astype(np.float32) for h in host])
+
+
 # ---------------------------------------------------------------- full size
 # The benchmark workload itself (rising thermal bubble, 128 x 256 x 256, the
 # launch configuration bench.py times).  The oracle runs on the whole grid: on
