@@ -250,8 +250,8 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
                                          const CF<R>& D, int hasD, const CF<double>& src, int has_src, R tau,
                                          const MF<R>& Rout, int i, int j, int k, int t) {
   const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
-  R mu = pick<R>(P.mu, P.mu_f), gm = pick<R>(P.gamma, P.gamma_f), h = R(0.5);
-  R ir = g.irc[i], is = g.isc[j];
+  R mu = pick<R>(P.mu, P.mu_f), gm = pick<R>(P.gamma, P.gamma_f);
+  R ir = g.irc[i];
   R accp = R(0), accT = R(0);
   R ap = R(0), aT = R(0);
 #pragma unroll
@@ -280,13 +280,15 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
   R divu;
   if constexpr (sizeof(R) == sizeof(double)) divu = div_ubar(gd, un, uk, i, j, k);
   else divu = div_ubar_ff(g, ub, ul, i, j, k);
-  R xrt = (htc<CIJ>(g, c, UT, i + 1, j, k) - htc<CIJ>(g, c, UT, i - 1, j, k)) * h * g.idr
-        + (hrc<CIJ>(g, c, UR, i, j + 1, k) - hrc<CIJ>(g, c, UR, i, j - 1, k)) * h * ir * g.idth;
-  R xrp = (hpc<CIJ>(g, c, UP, i + 1, j, k) - hpc<CIJ>(g, c, UP, i - 1, j, k)) * h * g.idr
-        + (hrc<CIJ>(g, c, UR, i, j, k + 1) - hrc<CIJ>(g, c, UR, i, j, k - 1)) * h * ir * is * g.idph;
-  R xtp = (hpc<CIJ>(g, c, UP, i, j + 1, k) - hpc<CIJ>(g, c, UP, i, j - 1, k)) * h * ir * g.idth
-        + (htc<CIJ>(g, c, UT, i, j, k + 1) - htc<CIJ>(g, c, UT, i, j, k - 1)) * h * ir * is * g.idph;
-  R cross = c.srt[t] * xrt + c.srp[t] * xrp + c.stp[t] * xtp;
+  // Cross terms of the viscous dissipation: the centred derivative sums
+  // d_r u_t + d_t u_r / r, d_r u_p + d_p u_r / (r sin), d_t u_p / r + d_p u_t / (r sin)
+  // of the centre-averaged velocities.  k_coef forms the same sums minus the
+  // metric terms u_t / r, u_p / r, u_p cot / r (S_rt, S_rp, S_tp, with the same
+  // accessors in the same tiles), so they are S + those terms.
+  R srt = c.srt[t], srp = c.srp[t], stp = c.stp[t];
+  R ut = htc<CIJ>(g, c, UT, i, j, k), up = hpc<CIJ>(g, c, UP, i, j, k);
+  R xrt = srt + ut * ir, xrp = srp + up * ir, xtp = stp + up * g.cotc[j] * ir;
+  R cross = srt * xrt + srp * xrp + stp * xtp;
   accp += -mu * (gm - R(1)) * cross;
   accT += -mu * c.beta[t] * cross;
   R Np = ap * divu + accp, NT = aT * divu + accT;
@@ -1416,9 +1418,7 @@ static int lines_attr() {
   const int sms = lines::NFS * lines::Shape<P, L, CB>::FS * (int)sizeof(float);
   if (cudaFuncSetAttribute(lines::k_lines_blk<D, P, L, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(lines::k_lines_sca<D, P, L, CB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(lines::k_lines_sca<D, P, L, CB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms) !=
+      cudaFuncSetAttribute(lines::k_lines_sca<D, P, L, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms) !=
           cudaSuccess)
     return SPH_ERR_CUDA;
   done = 1;
@@ -1475,22 +1475,19 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
   int ng, e;
   k_begin(c, SPH_K_SWEEP_R + D);
   if ((e = lines_attr<D, P, L, CB>())) return e;
-  if ((e = fork_aux(c, 2))) return e;
+  if ((e = fork_aux(c, 1))) return e;
   if ((ng = lines_groups(S, 0, NW)) > 0) {
     // one factor slot per warp
     if ((size_t)ng * SH::NWW * 32 * lines::slot_floats(P) > c->nscr) return SPH_ERR_ARG;
     lines::k_lines_blk<D, P, L, CB><<<ng, NT, smb, c->st>>>(S);
     c->launches++;
   }
-  if ((ng = lines_groups(S, 1, NW)) > 0) {
-    lines::k_lines_sca<D, P, L, CB, 1><<<ng, NT, sms, c->aux[0]>>>(S);
+  const int ng1 = lines_groups(S, 1, NW), ng2 = lines_groups(S, 2, NW);
+  if (ng1 + ng2 > 0) {
+    lines::k_lines_sca<D, P, L, CB><<<ng1 + ng2, NT, sms, c->aux[0]>>>(S, ng1);
     c->launches++;
   }
-  if ((ng = lines_groups(S, 2, NW)) > 0) {
-    lines::k_lines_sca<D, P, L, CB, 2><<<ng, NT, sms, c->aux[1]>>>(S);
-    c->launches++;
-  }
-  if ((e = join_aux(c, 2))) return e;
+  if ((e = join_aux(c, 1))) return e;
   c->launches--;  // launch_ok counts one more
   return launch_ok(c);
 }

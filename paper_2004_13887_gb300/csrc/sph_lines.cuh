@@ -591,9 +591,10 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
   flush_norms(S, ss, bad);
 }
 
-// Scalar lines of the transverse component trans_comp(D, KIND), n = L P, CB cells per block.
+// Scalar lines of the transverse component trans_comp(D, KIND), n = L P, CB
+// cells per block: line group grp of that kind.
 template <int D, int P, int L, int CB, int KIND>
-__global__ void __launch_bounds__(CB / P) k_lines_sca(SweepArgs<float> S) {
+__device__ __forceinline__ void lines_sca(const SweepArgs<float>& S, int grp) {
   using SH = Shape<P, L, CB>;
   constexpr int NW = SH::NW, NT = SH::NT, FS = SH::FS;
   constexpr int NI = P > 1 ? P - 1 : 1;
@@ -605,7 +606,7 @@ __global__ void __launch_bounds__(CB / P) k_lines_sca(SweepArgs<float> S) {
   const float h = S.h;
   float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
-  Group G = group_of(S, KIND, blockIdx.x, NW);
+  Group G = group_of(S, KIND, grp, NW);
 #pragma unroll
   for (int q = 0; q < P; q++) {
     int lw, c;
@@ -714,6 +715,14 @@ __global__ void __launch_bounds__(CB / P) k_lines_sca(SweepArgs<float> S) {
     }
   }
   flush_norms(S, ss, bad);
+}
+
+// Both transverse components of the sweep in one launch: blocks [0, ng1) take
+// the line groups of kind 1, the rest those of kind 2.
+template <int D, int P, int L, int CB>
+__global__ void __launch_bounds__(CB / P) k_lines_sca(SweepArgs<float> S, int ng1) {
+  if ((int)blockIdx.x < ng1) lines_sca<D, P, L, CB, 1>(S, blockIdx.x);
+  else lines_sca<D, P, L, CB, 2>(S, blockIdx.x - ng1);
 }
 
 }  // namespace lines
