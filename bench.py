@@ -48,9 +48,9 @@ HBM_PEAK_GBS = 6780.4     # measured copy bandwidth of the GB300s
 #   sweep_r/theta : rhs in (5 x 4 B) + Ubar in (5 x 4) + increment out (5 x 4)        =  60
 #   sweep_phi     : rhs in (5 x 4) + Ubar in (5 x 4) + U^k in and out (2 x 5 x 8)     = 120
 #   rhs           : U^n and U^k in (2 x 5 x 8) + R out (5 x 4)                         = 100
-#   coef          : Ubar in (5 x 4) + 14 coefficient planes out (14 x 4)               =  76
+#   coef          : Ubar in (5 x 4) + 17 coefficient planes out (17 x 4)               =  88
 #   avg           : U^n and U^k in (2 x 5 x 8) + Ubar out (5 x 4)                      = 100
-MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rhs": 100, "coef": 76, "avg": 100}
+MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rhs": 100, "coef": 88, "avg": 100}
 
 # DRAM traffic of each mixed stage measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the stage's launches, per grid point, the mean of

@@ -154,6 +154,10 @@ __device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<
   c.srt[t] = grt + gtr;
   c.srp[t] = grp + gpr;
   c.stp[t] = gtp + gpt;
+  c.dvr[t] = (g.rf[i + 1] * g.rf[i + 1] * UR[IRf(g, i + 1, j, k)] - g.rf[i] * g.rf[i] * UR[IRf(g, i, j, k)]) * ir * ir
+           * g.idr;
+  c.dvt[t] = (g.sf[j + 1] * UT[ITf(g, i, j + 1, k)] - g.sf[j] * UT[ITf(g, i, j, k)]) * ir * is * g.idth;
+  c.dvp[t] = (vp<CIJ>(g, UP, i, j, k + 1) - vp<CIJ>(g, UP, i, j, k)) * ir * is * g.idph;
 }
 
 // The stencil kernels run on tiles of TK x TJ x TI points (phi fastest; 128
@@ -336,16 +340,16 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     R bf = sdiv(c.drho[c0] + c.drho[c1], rs);
     acc += (R(1) - bf) * g.ehyd[i] + pick<R>(P.g, P.g_f) * bf;
     // D_M
-    R irf = g.irf[i], s = g.sc[j], is = g.isc[j];
+    R irf = g.irf[i], s = g.sc[j];
     R irh = sdiv(R(2), rs);
     R utf = h * (htc<CIJ>(g, c, UT, i - 1, j, k) + htc<CIJ>(g, c, UT, i, j, k));
     R upf = h * (hpc<CIJ>(g, c, UP, i - 1, j, k) + hpc<CIJ>(g, c, UP, i, j, k));
+    // theta and phi parts of div(Ubar) at the centres i - 1, i
     R Q[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
-      int m = i - 1 + q;
-      Q[q] = (g.sf[j + 1] * UT[ITf(g, m, j + 1, k)] - g.sf[j] * UT[ITf(g, m, j, k)]) * g.irc[m] * is * g.idth
-           + (vp<CIJ>(g, UP, m, j, k + 1) - vp<CIJ>(g, UP, m, j, k)) * g.irc[m] * is * g.idph;
+      int cm = IC(g, i - 1 + q, j, k);
+      Q[q] = c.dvt[cm] + c.dvp[cm];
     }
     acc += -utf * utf * irf - upf * upf * irf + R(2) * mu * irh * UR[t] * irf * irf - R(2) * om * s * upf
          - mu * irh * R(1.0 / 3.0) * g.idr * (Q[1] - Q[0]) + mu * irh * irf * (Q[0] + Q[1]);
@@ -363,15 +367,15 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     R ubt = UT[t];
     R upf = h * (hpc<CIJ>(g, c, UP, i, j - 1, k) + hpc<CIJ>(g, c, UP, i, j, k));
     R vrf = h * (hrc<CIJ>(g, c, UR, i, j - 1, k) + hrc<CIJ>(g, c, UR, i, j, k));
+    // r and phi parts of div(Ubar) at the centres j - 1, j; dpf = the mean of
+    // their d_p u_p (the phi part times r sin)
     R Dr[2], Dp[2], dpf = R(0);
 #pragma unroll
     for (int q = 0; q < 2; q++) {
-      int m = j - 1 + q;
-      Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * UR[IRf(g, i + 1, m, k)] - g.rf[i] * g.rf[i] * UR[IRf(g, i, m, k)])
-            * ir * ir * g.idr;
-      R dv = vp<CIJ>(g, UP, i, m, k + 1) - vp<CIJ>(g, UP, i, m, k);
-      Dp[q] = dv * ir * g.isc[m] * g.idph;
-      dpf += h * dv * g.idph;
+      int m = j - 1 + q, cm = IC(g, i, m, k);
+      Dr[q] = c.dvr[cm];
+      Dp[q] = c.dvp[cm];
+      dpf += h * Dp[q] * g.rc[i] * g.sc[m];
     }
     acc += ubt * vrf * ir - upf * upf * cotf * ir + mu * irh * ubt * ir * ir * isfj * isfj - R(2) * om * cfj * upf
          - mu * irh * R(1.0 / 3.0) * ir * g.idth * ((Dr[1] - Dr[0]) + (Dp[1] - Dp[0]))
@@ -391,13 +395,16 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
     R ubp = UP[t];
     R vrf = h * (hrc<CIJ>(g, c, UR, i, j, k - 1) + hrc<CIJ>(g, c, UR, i, j, k));
     R vtf = h * (htc<CIJ>(g, c, UT, i, j, k - 1) + htc<CIJ>(g, c, UT, i, j, k));
+    // r and theta parts of div(Ubar) at the centres k - 1, k (interior faces: real
+    // centres, wrapped on a periodic line)
     R Dr[2], Dt[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) {
       int m = k - 1 + q;
-      Dr[q] = (g.rf[i + 1] * g.rf[i + 1] * vr<CIJ>(g, UR, i + 1, j, m) - g.rf[i] * g.rf[i] * vr<CIJ>(g, UR, i, j, m))
-            * ir * ir * g.idr;
-      Dt[q] = (g.sf[j + 1] * vt<CIJ>(g, UT, i, j + 1, m) - g.sf[j] * vt<CIJ>(g, UT, i, j, m)) * ir * is * g.idth;
+      if (g.per) m = wrapk(g, m);
+      int cm = IC(g, i, j, m);
+      Dr[q] = c.dvr[cm];
+      Dt[q] = c.dvt[cm];
     }
     acc += ubp * vtf * cot * ir + ubp * vrf * ir + mu * irh * ubp * ir * ir * is * is + R(2) * om * (cj * vtf + s * vrf)
          - mu * irh * R(1.0 / 3.0) * ir * is * g.idph * ((Dr[1] - Dr[0]) + (Dt[1] - Dt[0]))
@@ -1030,6 +1037,7 @@ static int bufs_alloc(Bufs<R>& b, size_t nmet, int nr, const size_t* nf, long N,
   cf.Pb = q; cf.Tb = q + N; cf.rho = q + 2 * N; cf.drho = q + 3 * N; cf.beta = q + 4 * N; cf.uc0 = q + 5 * N;
   cf.uc1 = q + 6 * N; cf.uc2 = q + 7 * N; cf.grr = q + 8 * N; cf.gtt = q + 9 * N; cf.gpp = q + 10 * N;
   cf.srt = q + 11 * N; cf.srp = q + 12 * N; cf.stp = q + 13 * N;
+  cf.dvr = q + 14 * N; cf.dvt = q + 15 * N; cf.dvp = q + 16 * N;
   return SPH_OK;
 }
 

@@ -136,8 +136,12 @@ template <typename R>
 struct Coef {  // per cell centre, frozen at Ubar
   R *Pb, *Tb, *rho, *drho, *beta, *uc0, *uc1, *uc2;
   R *grr, *gtt, *gpp, *srt, *srp, *stp;  // G_rr, G_tt, G_pp, G_rt+G_tr, G_rp+G_pr, G_tp+G_pt
+  // the three parts of div(Ubar) at the centre, (1/r^2) d_r (r^2 u_r),
+  // (1/(r sin)) d_t (sin u_t), (1/(r sin)) d_p u_p, for the grad-div viscous
+  // terms of the momentum rows (each row reads them at its two centres)
+  R *dvr, *dvt, *dvp;
 };
-constexpr int NCOEF = 14;
+constexpr int NCOEF = 17;
 
 template <typename R> struct CF { const R* f[5]; };
 template <typename R> struct MF { R* f[5]; };
