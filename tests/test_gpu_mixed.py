@@ -125,6 +125,19 @@ def test_mixed_steps_full_size_bubble():
         assert v <= 1e-6, (k, v)
 
 
+def test_mixed_steps_full_size_200():
+    """The benchmark workload for the 200 steps it is defined with: mixed vs
+    FP64 per physical field (relative L2) stays within 1e-6."""
+    c = cases.bubble((128, 256, 256), seed=1, dt=1.0)
+    U64, U32 = run_both(c, 200)
+    A, B = physical_fields(U32, c.bg, c.par), physical_fields(U64, c.bg, c.par)
+    errs = {k: l2_rel(A[k], B[k]) for k in ("p", "rho", "theta", "T")}
+    errs["u"] = velocity_l2(A, B)
+    print("mixed vs fp64, 200 steps:", errs)
+    for k, v in errs.items():
+        assert v <= 1e-6, (k, v)
+
+
 # Line lengths 64, 128, 256 in every direction (16 lanes per line with chunks
 # of 4 and 8 cells, 32 lanes with chunks of 8), periodic and walled phi, a
 # pole, directions of other lengths (block Thomas) next to partitioned ones,
