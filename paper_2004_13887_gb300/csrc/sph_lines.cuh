@@ -52,24 +52,25 @@ constexpr unsigned FULL = 0xffffffffu;
 // per-lane floats of a block-line factor slot: (E, g, H) per interior cell
 __host__ __device__ constexpr int slot_floats(int P) { return (P > 1 ? P - 1 : 1) * NFAC; }
 
-// Shape of a launch: lines of n = L P cells, L lanes per line (32, or 16 so
-// that a warp holds two lines), P cells per lane; a block holds NW lines and
-// CB of their cells (NT = CB / P threads, NWW warps).  In shared memory each
-// staged field is 32 rows of CB/32 values and one word of padding (LS), FS
-// floats in all.
+// Shape of a launch: lines of n = L P cells, L lanes per line (16 or 32, or
+// 64 and 128 for lines spanning 2 and 4 warps), P cells per lane; a block
+// holds NW lines and CB of their cells (NT = CB / P threads, NWW warps; thread
+// w L + l takes lane l of block line w).  In shared memory each staged field
+// is 32 rows of CB/32 values and one word of padding (LS), FS floats in all.
 template <int P, int L, int CB>
 struct Shape {
-  static constexpr int n = L * P, NW = CB / n, NT = CB / P, NWW = NT / 32, LPW = 32 / L;
+  static constexpr int n = L * P, NW = CB / n, NT = CB / P, NWW = NT / 32;
   static constexpr int LS = CB / 32 + 1, FS = 32 * LS;
 };
 
-// position in shared memory of cell c on block line w: the chunk of lane l of
-// the warp holding the line is one padded row, so that the lanes of a warp
+// position in shared memory of cell c on block line w: the chunk of each
+// thread is spread over its lane's padded row, so that the lanes of a warp
 // reading one cell each of their chunks hit 32 distinct banks
 template <int P, int L, int CB>
 __device__ __forceinline__ int sidx(int w, int c) {
   using S = Shape<P, L, CB>;
-  return ((w % S::LPW) * L + c / P) * S::LS + (c % P) * S::NWW + w / S::LPW;
+  const int tid = w * L + c / P;
+  return (tid % 32) * S::LS + (c % P) * S::NWW + tid / 32;
 }
 
 // element e of a block's staging pass -> (line w, cell c): lines adjacent in
@@ -142,6 +143,27 @@ __device__ __forceinline__ void shfl_get(const float* s, float* o, int src, bool
   }
 }
 
+// The same for any L: a line of more than 32 lanes spans several warps, and its
+// lanes exchange through the shared buffer xb (NS x blockDim.x floats; every
+// thread of the block takes part, between two block barriers).
+template <int NS, int L>
+__device__ __forceinline__ void xget(const float* s, float* o, int src, bool zero, float* xb) {
+  if constexpr (L <= 32) {
+    shfl_get<NS, L>(s, o, src, zero);
+  } else {
+    const int nt = blockDim.x, tid = threadIdx.x, base = tid - tid % L;
+#pragma unroll
+    for (int q = 0; q < NS; q++) xb[q * nt + tid] = s[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NS; q++) {
+      float v = xb[q * nt + base + src];
+      o[q] = zero ? 0.f : v;
+    }
+    __syncthreads();
+  }
+}
+
 // X <- B^-1 (A, C, r)
 __device__ __forceinline__ void normalise3(const float* A, const float* B, const float* C, const float* r, float* X,
                                            int* bad) {
@@ -163,11 +185,11 @@ __device__ __forceinline__ void normalise3(const float* A, const float* B, const
 // l ^ L/2 (both sides of a cyclic line meet there; on a non-cyclic line one of
 // A, C is zero):  x + M x_p = r,  x_p + M_p x = r_p  =>  (I - M M_p) x = r - M r_p.
 template <int L>
-__device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int* bad) {
+__device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int* bad, float* xb) {
 #pragma unroll 1
   for (int s = 1; s < L / 2; s <<= 1) {
     float o[NR3], A[9], B[9], C[9], r[3], t[9], u[3];
-    shfl_get<NR3, L>(X, o, (lane - s) & (L - 1), !cyc && lane < s);
+    xget<NR3, L>(X, o, (lane - s) & (L - 1), !cyc && lane < s, xb);
     mm3(X, o + 9, t);
 #pragma unroll
     for (int q = 0; q < 9; q++) B[q] = (q % 4 == 0 ? 1.f : 0.f) - t[q];
@@ -177,7 +199,7 @@ __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int*
     mv3(X, o + 18, u);
 #pragma unroll
     for (int q = 0; q < 3; q++) r[q] = X[18 + q] - u[q];
-    shfl_get<NR3, L>(X, o, (lane + s) & (L - 1), !cyc && lane + s > L - 1);
+    xget<NR3, L>(X, o, (lane + s) & (L - 1), !cyc && lane + s > L - 1, xb);
     mm3(X + 9, o, t);
 #pragma unroll
     for (int q = 0; q < 9; q++) B[q] -= t[q];
@@ -194,7 +216,7 @@ __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int*
   for (int z = 0; z < 9; z++) M[z] = X[z] + X[9 + z];
 #pragma unroll
   for (int z = 0; z < 3; z++) M[9 + z] = X[18 + z];
-  shfl_get<12, L>(M, ph, lane ^ (L / 2), false);
+  xget<12, L>(M, ph, lane ^ (L / 2), false, xb);
   float Sm[9], Si[9], rr[3], u[3];
   mm3(M, ph, Sm);
 #pragma unroll
@@ -208,16 +230,13 @@ __device__ __forceinline__ void pcr3(float* X, int lane, int cyc, float* x, int*
 
 // The same for the scalar reduced system (a x_{l-s} + x_l + c x_{l+s} = r).
 template <int L>
-__device__ __forceinline__ float pcr1(float a, float c, float r, int lane, int cyc, int* bad) {
+__device__ __forceinline__ float pcr1(float a, float c, float r, int lane, int cyc, int* bad, float* xb) {
 #pragma unroll 1
   for (int s = 1; s < L / 2; s <<= 1) {
-    int lo = (lane - s) & (L - 1), up = (lane + s) & (L - 1);
-    float la = __shfl_sync(FULL, a, lo, L), lc = __shfl_sync(FULL, c, lo, L);
-    float lr = __shfl_sync(FULL, r, lo, L);
-    float ua = __shfl_sync(FULL, a, up, L), uc = __shfl_sync(FULL, c, up, L);
-    float ur = __shfl_sync(FULL, r, up, L);
-    if (!cyc && lane < s) la = lc = lr = 0.f;
-    if (!cyc && lane + s > L - 1) ua = uc = ur = 0.f;
+    float v[3] = {a, c, r}, lv[3], uv[3];
+    xget<3, L>(v, lv, (lane - s) & (L - 1), !cyc && lane < s, xb);
+    xget<3, L>(v, uv, (lane + s) & (L - 1), !cyc && lane + s > L - 1, xb);
+    float la = lv[0], lc = lv[1], lr = lv[2], ua = uv[0], uc = uv[1], ur = uv[2];
     float b = 1.f - a * lc - c * ua;
     if (b == 0.f || !isfinite(b)) *bad |= FLAG_SINGULAR;
     float ib = sdiv(1.f, b);
@@ -226,7 +245,9 @@ __device__ __forceinline__ float pcr1(float a, float c, float r, int lane, int c
     a = an; c = cn;
   }
   float M = a + c;
-  float Mp = __shfl_sync(FULL, M, lane ^ (L / 2), L), rp = __shfl_sync(FULL, r, lane ^ (L / 2), L);
+  float mr[2] = {M, r}, pr[2];
+  xget<2, L>(mr, pr, lane ^ (L / 2), false, xb);
+  float Mp = pr[0], rp = pr[1];
   float den = 1.f - M * Mp;
   if (den == 0.f || !isfinite(den)) *bad |= FLAG_SINGULAR;
   return sdiv(r - M * rp, den);
@@ -325,11 +346,12 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
   const Geo<float>& g = S.g;
   const int n = SH::n, cyc = (D == 2 && g.per);
   const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;  // warp, lane of the warp
-  const int w = wid * SH::LPW + wl / L, lane = wl % L;      // block line, lane of the line
+  const int w = threadIdx.x / L, lane = threadIdx.x % L;    // block line, lane of the line
   const float h = S.h;
   float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
   float* slot = S.scr + ((size_t)blockIdx.x * SH::NWW + wid) * (32 * slot_floats(P));
+  float* xb = sm + 3 * FS;  // lane exchanges of lines longer than a warp (after the elimination)
   Group G = group_of(S, 0, blockIdx.x, NW);
   // 1. stage (n NW = P NT elements: P per thread, all copies in flight).  The
   // block lines past the group's last repeat it, so that every lane of a warp
@@ -466,12 +488,15 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
     }
     if (P > 1) {
       // x_0 = p + Q X_l + W X_{l-1} (the elimination's last interior cell had x_{t+1} = X_l)
-      // separator row: x_{s+1} = p' + Q' X_{l+1} + W' X_l from lane l+1
+      // separator row: x_{s+1} = p' + Q' X_{l+1} + W' X_l from lane l+1 (lines
+      // longer than a warp exchange through the staged fields 3-10, dead now
+      // that every lane has eliminated its chunk)
       float pn[3], Qn[9], Wn[9], T9[9], u[3];
       bool none = !cyc && lane == L - 1;
-      shfl_get<3, L>(p, pn, (lane + 1) & (L - 1), none);
-      shfl_get<9, L>(Q, Qn, (lane + 1) & (L - 1), none);
-      shfl_get<9, L>(W, Wn, (lane + 1) & (L - 1), none);
+      if (L > 32) __syncthreads();
+      xget<3, L>(p, pn, (lane + 1) & (L - 1), none, xb);
+      xget<9, L>(Q, Qn, (lane + 1) & (L - 1), none, xb);
+      xget<9, L>(W, Wn, (lane + 1) & (L - 1), none, xb);
       mm3_C(Xs + 9, Wn, T9);
 #pragma unroll
       for (int q = 0; q < 9; q++) Bs[q] += T9[q];
@@ -490,8 +515,8 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
     }
     // 3. reduced system
     float xs[3], xp[3];
-    pcr3<L>(Xs, lane, cyc, xs, &bad);
-    shfl_get<3, L>(xs, xp, (lane + L - 1) & (L - 1), !cyc && lane == 0);
+    pcr3<L>(Xs, lane, cyc, xs, &bad, xb);
+    xget<3, L>(xs, xp, (lane + L - 1) & (L - 1), !cyc && lane == 0, xb);
     // 4. back substitution; each lane writes its increments over its own
     // staged inputs (fields 0-2), which only it reads
     int sl = sidx<P, L, CB>(w, lane * P + P - 1);
@@ -602,7 +627,8 @@ __device__ __forceinline__ void lines_sca(const SweepArgs<float>& S, int grp) {
   extern __shared__ float sm[];
   const Geo<float>& g = S.g;
   const int n = SH::n, cyc = (D == 2 && g.per);
-  const int w = (threadIdx.x >> 5) * SH::LPW + (threadIdx.x & 31) / L, lane = (threadIdx.x & 31) % L;
+  const int w = threadIdx.x / L, lane = threadIdx.x % L;
+  float* xb = sm + FS;  // lane exchanges of lines longer than a warp (after the elimination)
   const float h = S.h;
   float ss[5] = {0, 0, 0, 0, 0};
   int bad = 0;
@@ -657,19 +683,19 @@ __device__ __forceinline__ void lines_sca(const SweepArgs<float>& S, int grp) {
         W = -h_[t] - e_[t] * W;
       }
       bool none = !cyc && lane == L - 1;
-      int up = (lane + 1) & (L - 1);
-      float pn = __shfl_sync(FULL, p, up, L), Qn = __shfl_sync(FULL, Q, up, L);
-      float Wn = __shfl_sync(FULL, W, up, L);
-      if (none) pn = Qn = Wn = 0.f;
+      float pqw[3] = {p, Q, W}, nx[3];
+      if (L > 32) __syncthreads();
+      xget<3, L>(pqw, nx, (lane + 1) & (L - 1), none, xb);
+      float pn = nx[0], Qn = nx[1], Wn = nx[2];
       sb += sc * Wn;
       sr -= sc * pn;
       sc = sc * Qn;
     }
     if (sb == 0.f || !isfinite(sb)) bad |= FLAG_SINGULAR;
     float ib = sdiv(1.f, sb);
-    float xs = pcr1<L>(sa * ib, sc * ib, sr * ib, lane, cyc, &bad);
-    float xp = __shfl_sync(FULL, xs, (lane + L - 1) & (L - 1), L);
-    if (!cyc && lane == 0) xp = 0.f;
+    float xs = pcr1<L>(sa * ib, sc * ib, sr * ib, lane, cyc, &bad, xb);
+    float xp;
+    xget<1, L>(&xs, &xp, (lane + L - 1) & (L - 1), !cyc && lane == 0, xb);
     float xo[P];
     xo[P - 1] = xs;
 #pragma unroll

@@ -138,12 +138,14 @@ def test_mixed_steps_full_size_200():
         assert v <= 1e-6, (k, v)
 
 
-# Line lengths 64, 128, 256 in every direction (16 lanes per line with chunks
+# Line lengths 64 to 1024 in every direction (16 lanes per line with chunks
 # of 4 and 8 cells, 32 lanes with chunks of 8), periodic and walled phi, a
 # pole, directions of other lengths (block Thomas) next to partitioned ones,
 # and line counts that leave the last group of a launch partly empty (r lines
 # of 64, 128 and 256 cells in groups of 16, 8 and 8; theta lines of 256 in
-# groups of 8; cyclic phi lines of 128 in groups of 8).
+# groups of 8; cyclic phi lines of 128 in groups of 8).  Phi lines of 512 and
+# 1024 cells span 2 and 4 warps (walled with a partial group of 4 lines,
+# cyclic); r and theta lines of 512 and 1024 take block Thomas.
 PART_CASES = {
     "bubble_64x64x128": lambda: _bubble((64, 64, 128)),
     "shell_64x128x256": lambda: _shell((64, 128, 256), pole=False),
@@ -154,6 +156,10 @@ PART_CASES = {
     "shell_40x36x128": lambda: _shell((40, 36, 128), pole=False),
     "sector_40x256x20": lambda: _sector((40, 256, 20)),
     "bubble_256x20x12": lambda: _bubble((256, 20, 12)),
+    "shell_16x512x1024": lambda: _shell((16, 512, 1024), pole=False),
+    "sector_16x1024x41": lambda: _sector((16, 1024, 41)),
+    "bubble_16x38x512": lambda: _bubble((16, 38, 512)),
+    "sector_512x8x13": lambda: _sector((512, 8, 13)),
 }
 
 
