@@ -4,25 +4,32 @@
 // chapter3mainsd, splitting2, spl1-spl3), MAC grid in spherical coordinates,
 // operators of Appendix B.
 //
-// One iteration k -> k+1 is five launches:
-//   avg   : Ubar = (U^n + U^{n+1,k})/2 in the bulk type
+// One iteration k -> k+1 is six stages:
+//   avg   : Ubar = (U^n + U^{n+1,k})/2 in the bulk type, and D = U^k - U^n
 //   coef  : per-centre coefficients frozen at Ubar (p+pi_inf, T, rho, rho-rho_ref,
-//           beta, centre velocities, grad u with metric terms)
+//           beta, centre velocities, grad u with metric terms, the three parts
+//           of div Ubar)
 //   rhs   : R = -(U^k - U^n) - tau [N(Ubar) + G - S]  (the right-hand side of
 //           eq. spl1 after the linearity of D(Ubar) is used: the D(U^k - U^n),
-//           D U^n and D_M terms collapse to the full operator at Ubar)
+//           D U^n and D_M terms collapse to the full operator at Ubar); four
+//           launches: centre rows (p, T) and the three momentum rows
 //   sweep : r, theta, phi line solves (I + tau/2 D_d) x = rhs (eqs. spl1-spl3):
-//           one thread per line, 3x3-block Thomas for (p, T, u_d) and scalar
-//           Thomas for the two transverse velocities; cyclic lines (periodic phi)
-//           by a rank-3 Woodbury / Sherman-Morrison correction.  The phi sweep
-//           also applies U^{k+1} = U^k + x and accumulates the increment norm.
+//           3x3-block systems for (p, T, u_d), scalar ones for the two
+//           transverse velocities, cyclic along a periodic phi.  FP64 mode: one
+//           thread per line (block Thomas, Woodbury / Sherman-Morrison on cyclic
+//           lines).  Mixed mode: the partitioned solver of sph_lines.cuh (lanes
+//           of a warp per line, chunk elimination + parallel cyclic reduction),
+//           one launch for the block lines and one for both transverse kinds.
+//           The phi sweep also applies U^{k+1} = U^k + x and accumulates the
+//           increment norm.
 //
 // Precision: everything is templated on the bulk type R.  R = double is the
-// plain FP64 scheme.  R = float ("mixed") keeps U^n, U^{n+1,k}, their update and
-// the -(U^k - U^n) part of R in FP64, forms div(Ubar) -- which multiplies
-// gamma (p + pi_inf) and nearly cancels at low Mach number -- in FP64 from the
-// FP64 state, writes the hydrostatic part of the r-momentum row through density
-// perturbations, and combines the cyclic corrections in FP64.
+// plain FP64 scheme.  R = float ("mixed") keeps U^n, U^{n+1,k} and their update
+// in FP64 and everything per iteration in FP32: Ubar and D are formed from the
+// FP64 state as hi + lo pairs on the FP32 pipe, div(Ubar) -- which multiplies
+// gamma (p + pi_inf) and nearly cancels at low Mach number -- is carried as a
+// pair, the hydrostatic part of the r-momentum row goes through density
+// perturbations, and the cyclic corrections of the Thomas path combine in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
