@@ -161,8 +161,9 @@ int sph_set_line_solver(sph_ctx* ctx, int which);
 long long sph_launch_count(const sph_ctx* ctx);
 
 /* Per-kernel timing.  sph_profile(ctx, 1) clears the record and starts timing
- * every kernel stage (one launch, or the one to three launches of a
- * partitioned sweep) with a pair of CUDA events on the context's stream; 0
+ * every kernel stage (one launch, the four of the right-hand side, or the
+ * two of a partitioned sweep) with a pair of CUDA events on the context's
+ * stream, around the side streams' work; 0
  * stops.  sph_profile_read synchronises the stream and writes, for each kernel
  * kind SPH_K_* (SPH_NKERNELS entries), the summed duration in ms and the stage
  * count (either pointer may be NULL).  At most 65536 stages are recorded;
