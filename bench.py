@@ -57,8 +57,8 @@ MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rh
 # the two Picard iterations of a step; profiles/stages_bubble_128x256x256_mixed.md)
 # and the hash of the kernel sources it was measured on: reported only while
 # the sources match.
-MEASURED_TRAFFIC = {"avg": 98.1, "coef": 81.7, "rhs": 201.2, "sweep_r": 75.9, "sweep_theta": 80.3, "sweep_phi": 141.0}
-TRAFFIC_SOURCE_HASH = "3f1bdec6f3da150b"
+MEASURED_TRAFFIC = {"avg": 98.1, "coef": 81.7, "rhs": 201.2, "sweep_r": 75.8, "sweep_theta": 80.3, "sweep_phi": 141.1}
+TRAFFIC_SOURCE_HASH = "8bc7eb1b6197b443"
 
 
 def kernel_source_hash():
@@ -426,7 +426,7 @@ def run_ensemble(args, rank, world, dist):
                                    "nr in {16,32,48,64}, n_theta and n_phi in {64,128,192,256}, amplitude 0.2-1 K, "
                                    "radius 1-3 km, K=2, dt=1 s, one CUDA graph per two steps",
                        "instances": len(cs), "points": pts, "shapes": shapes,
-                       "line_solver": {f"{k[0]}x{k[1]}x{k[2]}": ("partitioned" if v else "thomas")
+                       "line_solver": {f"{k[0]}x{k[1]}x{k[2]}": ({0: "thomas", 1: "partitioned", 2: "partitioned_warp"}[v])
                                        for k, v in ens.choice.items()},
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": "whole step (all stages)", "unit": "GB/s", "peak": HBM_PEAK_GBS,

@@ -144,8 +144,8 @@ def test_mixed_steps_full_size_200():
 # and line counts that leave the last group of a launch partly empty (r lines
 # of 64, 128 and 256 cells in groups of 16, 8 and 8; theta lines of 256 in
 # groups of 8; cyclic phi lines of 128 in groups of 8).  Phi lines of 512 and
-# 1024 cells span 2 and 4 warps (walled with a partial group of 4 lines,
-# cyclic); r and theta lines of 512 and 1024 take block Thomas.
+# 1024 cells span 2 and 4 warps (walled and cyclic, with partial groups of 4
+# lines); r and theta lines of 512 and 1024 take block Thomas.
 PART_CASES = {
     "bubble_64x64x128": lambda: _bubble((64, 64, 128)),
     "shell_64x128x256": lambda: _shell((64, 128, 256), pole=False),
@@ -159,6 +159,7 @@ PART_CASES = {
     "shell_16x512x1024": lambda: _shell((16, 512, 1024), pole=False),
     "sector_16x1024x41": lambda: _sector((16, 1024, 41)),
     "bubble_16x38x512": lambda: _bubble((16, 38, 512)),
+    "shell_16x66x512": lambda: _shell((16, 66, 512), pole=False),
     "sector_512x8x13": lambda: _sector((512, 8, 13)),
 }
 
