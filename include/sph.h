@@ -138,16 +138,16 @@ int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double
 
 /* Line solver of the sweeps in SPH_PREC_MIXED mode (eqs. spl1-spl3 leave the
  * method of solving each line open; Section 2.2 names the block Thomas
- * algorithm).  SPH_LINES_PARTITIONED (the default): for lines of 64, 128 or
- * 256 cells, and phi lines of 512 or 1024, a segment of lanes per line -- each
- * lane eliminates a chunk of the line, the chunk-boundary unknowns are solved
- * by parallel cyclic reduction across the segment, then each lane
- * back-substitutes; lines of 64 and 128 cells take 16 lanes (two lines per
- * warp, chunks of 4 and 8 cells), lines of 256 take 32, phi lines of 512 and
- * 1024 take 64 and 128 lanes (2 and 4 warps, chunks of 8); other lines use
- * the block Thomas path.
+ * algorithm).  SPH_LINES_PARTITIONED (the default): for lines of 16, 32, 48,
+ * 64, 128, 192 or 256 cells, and phi lines of 512 or 1024, a segment of lanes
+ * per line -- each lane eliminates a chunk of the line, the chunk-boundary
+ * unknowns are solved by parallel cyclic reduction across the segment, then
+ * each lane back-substitutes; lines of up to 128 cells take 16 lanes (two
+ * lines per warp, chunks of 1 to 8 cells), lines of 192 and 256 take 32
+ * (chunks of 6 and 8), phi lines of 512 and 1024 take 64 and 128 lanes (2 and
+ * 4 warps, chunks of 8); other lines use the block Thomas path.
  * SPH_LINES_PARTITIONED_WARP: the same with 32 lanes (one line per warp) for
- * the lines of up to 256 cells.  SPH_LINES_THOMAS: block (and scalar) Thomas, one thread per
+ * the lines of 64 and 128 cells.  SPH_LINES_THOMAS: block (and scalar) Thomas, one thread per
  * line, with the Woodbury / Sherman-Morrison correction on cyclic lines.  All
  * give the exact solution up to rounding (no pivoting between blocks in any).
  * The FP64 mode always uses block Thomas.  Returns SPH_ERR_ARG for other

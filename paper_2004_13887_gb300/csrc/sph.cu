@@ -1442,8 +1442,11 @@ static int lines_attr() {
 
 // cells per block of the partitioned solver: 2048 for 256-cell lines along r
 // and theta (8 adjacent lines per block fill each 32-byte sector) and for the
-// phi lines of 512 and 1024 cells (4 and 2 lines a block), else 1024
-__host__ __device__ constexpr int lines_cb(int D, int n) { return n >= 512 || (D != 2 && n == 256) ? 2048 : 1024; }
+// phi lines of 512 and 1024 cells (4 and 2 lines a block); 512, 768 and 1536
+// for lines of 16, 48 and 192 cells (32, 16 and 8 lines); else 1024
+__host__ __device__ constexpr int lines_cb(int D, int n) {
+  return n == 16 ? 512 : n == 48 ? 768 : n == 192 ? 1536 : n >= 512 || (D != 2 && n == 256) ? 2048 : 1024;
+}
 
 static int lines_groups(const SweepArgs<float>& S, int kind, int NW) {
   if (S.nl[kind] <= 0) return 0;
@@ -1460,14 +1463,16 @@ static size_t lines_scratch(int nr, int nt, int np, int per) {
   size_t mx = 0;
   for (int d = 0; d < 3; d++) {
     int n = d == 0 ? nr : d == 1 ? nt : np;
-    if (n != 64 && n != 128 && n != 256 && !(d == 2 && (n == 512 || n == 1024))) continue;
+    if (n != 16 && n != 32 && n != 48 && n != 64 && n != 128 && n != 192 && n != 256 &&
+        !(d == 2 && (n == 512 || n == 1024)))
+      continue;
     SweepArgs<float> S;
     memset(&S, 0, sizeof S);
     line_layout(g, d, S);
     for (int L = 16; L <= 128; L *= 2) {
-      // the lane counts run_lines_d may take for n: 16 and 32 up to 128 cells,
-      // 32 for 256, n / 8 beyond
-      if (n <= 128 ? L > 32 : L != (n == 256 ? 32 : n / 8)) continue;
+      // the lane counts run_lines_d may take for n: 16 up to 48 cells; 16 and
+      // 32 for 64 and 128; 32 for 192 and 256; n / 8 beyond
+      if (n <= 48 ? L != 16 : n <= 128 ? L > 32 : L != (n <= 256 ? 32 : n / 8)) continue;
       int P = n / L, CB = lines_cb(d, n), NW = CB / n, NWW = CB / P / 32;
       size_t need = (size_t)lines_groups(S, 0, NW) * NWW * 32 * lines::slot_floats(P);
       if (need > mx) mx = need;
@@ -1476,16 +1481,17 @@ static size_t lines_scratch(int nr, int nt, int np, int per) {
   return mx;
 }
 
-// whether the partitioned solver takes the lines along d: lines of 64, 128 and
-// 256 cells, and phi lines of 512 and 1024 (one thread per line would read
-// those uncoalesced).  Along r and theta, lines of 512 cells run faster on the
+// whether the partitioned solver takes the lines along d: lines of 16, 32, 48,
+// 64, 128, 192 and 256 cells, and phi lines of 512 and 1024 (one thread per
+// line would read those uncoalesced).  Along r and theta, lines of 512 cells run faster on the
 // block Thomas path, whose threads read adjacent lines together (measured:
 // theta 4.3 vs 5.0 ms per step on 64 x 512 x 1024), and more accurately where
 // I + tau/2 D_r is stiff.
 static int lines_ok(const sph_ctx* c, int d) {
   const Geo<double>& g = c->d64.g;
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
-  return n == 64 || n == 128 || n == 256 || (d == 2 && (n == 512 || n == 1024));
+  return n == 16 || n == 32 || n == 48 || n == 64 || n == 128 || n == 192 || n == 256 ||
+         (d == 2 && (n == 512 || n == 1024));
 }
 
 template <int D, int P, int L>
@@ -1518,6 +1524,10 @@ static int run_lines(sph_ctx* c, SweepArgs<float>& S) {
 template <int D>
 static int lines_attr_d(int n) {
   int e = SPH_OK;
+  if (n == 16) e = lines_attr<D, 1, 16, lines_cb(D, 16)>();
+  if (n == 32) e = lines_attr<D, 2, 16, lines_cb(D, 32)>();
+  if (n == 48) e = lines_attr<D, 3, 16, lines_cb(D, 48)>();
+  if (n == 192) e = lines_attr<D, 6, 32, lines_cb(D, 192)>();
   if (n == 64 && !(e = lines_attr<D, 2, 32, lines_cb(D, 64)>())) e = lines_attr<D, 4, 16, lines_cb(D, 64)>();
   if (n == 128 && !(e = lines_attr<D, 4, 32, lines_cb(D, 128)>())) e = lines_attr<D, 8, 16, lines_cb(D, 128)>();
   if (n == 256) e = lines_attr<D, 8, 32, lines_cb(D, 256)>();
@@ -1536,11 +1546,16 @@ static int lines_prepare(const sph_ctx* c) {
   return e;
 }
 
-// lines of 64 and 128 cells: 16 lanes per line unless one warp per line is
-// asked for; 256: one warp; phi lines of 512 and 1024: 2 and 4 warps (chunks of 8)
+// lines of 16, 32, 48 cells: 16 lanes (chunks of 1, 2, 3); 64 and 128: 16
+// lanes unless one warp per line is asked for; 192 and 256: one warp (chunks
+// of 6, 8); phi lines of 512 and 1024: 2 and 4 warps (chunks of 8)
 template <int D>
 static int run_lines_d(sph_ctx* c, SweepArgs<float>& S, int n) {
   const int warp = c->line_solver == SPH_LINES_PARTITIONED_WARP;
+  if (n == 16) return run_lines<D, 1, 16>(c, S);
+  if (n == 32) return run_lines<D, 2, 16>(c, S);
+  if (n == 48) return run_lines<D, 3, 16>(c, S);
+  if (n == 192) return run_lines<D, 6, 32>(c, S);
   if (n == 64) return warp ? run_lines<D, 2, 32>(c, S) : run_lines<D, 4, 16>(c, S);
   if (n == 128) return warp ? run_lines<D, 4, 32>(c, S) : run_lines<D, 8, 16>(c, S);
   if constexpr (D == 2) {

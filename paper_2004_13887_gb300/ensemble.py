@@ -9,7 +9,7 @@ from . import SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMA
 
 
 def _partitioned_applies(grid) -> bool:
-    return any(n in (64, 128, 256) for n in (grid.nr, grid.nt, grid.np)) or grid.np in (512, 1024)
+    return any(n in (16, 32, 48, 64, 128, 192, 256) for n in (grid.nr, grid.nt, grid.np)) or grid.np in (512, 1024)
 
 
 def time_steps(solver, dt, n_iter, steps=2, warmup=1):

@@ -145,7 +145,10 @@ def test_mixed_steps_full_size_200():
 # of 64, 128 and 256 cells in groups of 16, 8 and 8; theta lines of 256 in
 # groups of 8; cyclic phi lines of 128 in groups of 8).  Phi lines of 512 and
 # 1024 cells span 2 and 4 warps (walled and cyclic, with partial groups of 4
-# lines); r and theta lines of 512 and 1024 take block Thomas.
+# lines); r and theta lines of 512 and 1024 take block Thomas.  Lines of 16,
+# 32, 48 and 192 cells (chunks of 1, 2, 3 on 16 lanes and of 6 on 32; walled
+# and cyclic, partial groups of 32 and 8 lines) are the short and mid lengths
+# of uneven ensembles.
 PART_CASES = {
     "bubble_64x64x128": lambda: _bubble((64, 64, 128)),
     "shell_64x128x256": lambda: _shell((64, 128, 256), pole=False),
@@ -160,6 +163,10 @@ PART_CASES = {
     "sector_16x1024x41": lambda: _sector((16, 1024, 41)),
     "bubble_16x38x512": lambda: _bubble((16, 38, 512)),
     "shell_16x66x512": lambda: _shell((16, 66, 512), pole=False),
+    "sector_16x48x192": lambda: _sector((16, 48, 192)),
+    "shell_32x20x192": lambda: _shell((32, 20, 192), pole=False),
+    "bubble_48x36x16": lambda: _bubble((48, 36, 16)),
+    "shell_16x40x16": lambda: _shell((16, 40, 16), pole=False),
     "sector_512x8x13": lambda: _sector((512, 8, 13)),
 }
 
