@@ -44,7 +44,7 @@
 namespace lines {
 
 constexpr int NFB = 11;       // staged fields of a block line
-constexpr int NFS = 4;        // staged fields of a scalar line
+constexpr int NFS = 5;        // staged fields of a scalar line
 constexpr int NFAC = 21;      // E (9), g (3), H (9) per interior cell
 constexpr int NR3 = 21;       // a normalised reduced row: A (0-8), C (9-17), r (18-20)
 constexpr unsigned FULL = 0xffffffffu;
@@ -293,19 +293,31 @@ __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm
   cpa4(sm + 9 * FS + si, S.rhs.f[4] + ic);
 }
 
-// stage the inputs of scalar-line cell c (component cc) of line (a, b); away
-// from the r and theta walls the averaged velocities come from the coefficient
-// planes without checks
+// stage the inputs of scalar-line cell c (component cc, on its face (i, j, k))
+// of line (a, b): rho at the face's two centres (fields 0, 1), the advecting
+// velocity u_D at those centres (fields 2, 3; the row takes their mean) and the
+// right-hand side (field 4).  Away from the r and theta walls these are plain
+// reads of the coefficient planes, copied asynchronously like the block
+// lines' inputs; next to them the checked accessors give rho and the mean,
+// which is stored twice (its mean is itself).
 template <int D, int KIND, int FS>
 __device__ __forceinline__ void stage_scalar(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c) {
   const Geo<float>& g = S.g;
   constexpr int cc = trans_comp(D, KIND);
   int i, j, k;
   line_pos(D, a, b, c, i, j, k);
-  SPt<float> q = inner_ij(g, i, j) ? load_s<false>(g, S.c, S.ub, cc, D, i, j, k)
-                                   : load_s<true>(g, S.c, S.ub, cc, D, i, j, k);
-  sm[0 * FS + si] = q.rho0; sm[1 * FS + si] = q.rho1; sm[2 * FS + si] = q.ua;
-  sm[3 * FS + si] = S.rhs.f[1 + cc][face_idx(g, cc, i, j, k)];
+  if (inner_ij(g, i, j)) {
+    int i0 = i - (cc == 0), j0 = j - (cc == 1), k0 = k - (cc == 2);
+    if (cc == 2 && g.per) k0 = wrapk(g, k0);  // k0 = -1 only on a periodic line
+    const int c0 = IC(g, i0, j0, k0), c1 = IC(g, i, j, k);
+    const float* ua = D == 0 ? S.c.uc0 : D == 1 ? S.c.uc1 : S.c.uc2;
+    cpa4(sm + 0 * FS + si, S.c.rho + c0); cpa4(sm + 1 * FS + si, S.c.rho + c1);
+    cpa4(sm + 2 * FS + si, ua + c0); cpa4(sm + 3 * FS + si, ua + c1);
+  } else {
+    SPt<float> q = load_s<true>(g, S.c, S.ub, cc, D, i, j, k);
+    sm[0 * FS + si] = q.rho0; sm[1 * FS + si] = q.rho1; sm[2 * FS + si] = q.ua; sm[3 * FS + si] = q.ua;
+  }
+  cpa4(sm + 4 * FS + si, S.rhs.f[1 + cc] + face_idx(g, cc, i, j, k));
 }
 
 // line group -> first line (a, bb) and the number of valid lines
@@ -639,6 +651,7 @@ __device__ __forceinline__ void lines_sca(const SweepArgs<float>& S, int grp) {
     elem<D, P, L, CB>(threadIdx.x + q * NT, lw, c);
     stage_scalar<D, KIND, FS>(S, sm, sidx<P, L, CB>(lw, c), G.a, G.bb + min(lw, G.nvalid - 1), c);  // see k_lines_blk
   }
+  cpa_wait_all();
   __syncthreads();
   {
     int a = G.a, b = G.bb + min(w, G.nvalid - 1);
@@ -649,8 +662,8 @@ __device__ __forceinline__ void lines_sca(const SweepArgs<float>& S, int grp) {
     for (int t = 0; t < P; t++) {
       int m = lane * P + t;
       int si = sidx<P, L, CB>(w, m);
-      SPt<float> q = {sm[si], sm[FS + si], sm[2 * FS + si]};
-      float r = sm[3 * FS + si];
+      SPt<float> q = {sm[si], sm[FS + si], 0.5f * (sm[2 * FS + si] + sm[3 * FS + si])};
+      float r = sm[4 * FS + si];
       int i, j, k;
       line_pos(D, a, b, m, i, j, k);
       float wt[3];
