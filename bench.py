@@ -57,6 +57,7 @@ MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rh
 # the two Picard iterations of a step; profiles/stages_bubble_128x256x256_mixed.md)
 # and the hash of the kernel sources it was measured on: reported only while
 # the sources match.
+TRAFFIC_GRID = (128, 256, 256)   # the workload the traffic below was measured on
 MEASURED_TRAFFIC = {"avg": 98.1, "coef": 81.7, "rhs": 201.2, "sweep_r": 75.8, "sweep_theta": 80.2, "sweep_phi": 141.0}
 TRAFFIC_SOURCE_HASH = "d008f83eb37e1e97"
 
@@ -295,7 +296,7 @@ def run_ours(args, rank, world, dist):
     per_launch_ms = dom_ms / max(dom_n, 1)
     bpp = MIXED_BYTES_PER_POINT.get(dom)
     traffic = None
-    if dom in MEASURED_TRAFFIC and TRAFFIC_SOURCE_HASH == kernel_source_hash():
+    if dom in MEASURED_TRAFFIC and TRAFFIC_SOURCE_HASH == kernel_source_hash() and tuple(GRID) == TRAFFIC_GRID:
         traffic = MEASURED_TRAFFIC[dom] * N   # bytes per stage launch
     roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "peak": HBM_PEAK_GBS,
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -337,7 +338,9 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": WORKLOAD, "grid": list(GRID), "K": K_ITER, "dt_s": DT,
                    "precision": "mixed: FP32 stencils and line solves; FP64 state, update, div u, cyclic corrections",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "no flush: the state (5 FP64 fields, 336 MB) and per-iteration buffers exceed the 129 MB L2"},
+                   "l2": (f"no flush: the state (5 FP64 fields, {nb / 1e6:.0f} MB) and per-iteration buffers "
+                          f"exceed the 129 MB L2" if nb > 129e6 else
+                          f"no flush: the state ({nb / 1e6:.0f} MB) fits the 129 MB L2 (small case)")},
         "roofline": roof,
         "kernel_shares": shares,
         "error_vs_fp64": errors,
