@@ -60,3 +60,30 @@ def test_no_cpu_fallback_without_library(tmp_path):
             pkg.load(str(tmp_path / "missing.so"))
         finally:
             pkg._lib = pkg._lib_backup
+
+
+def _defines():
+    vals = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            for name, v in re.findall(r"^#define\s+(SPH_[A-Z_0-9]+)\s+\(?(-?\d+)\)?\b", open(os.path.join(ROOT, "include", fn)).read(),
+                                      flags=re.M):
+                vals[name] = int(v)
+    return vals
+
+
+def test_binding_constants_match_header():
+    """Every SPH_* constant of the Python binding has the header's value, and the
+    stage names it reports follow the header's SPH_K_* order."""
+    import paper_2004_13887_gb300 as pkg
+    d = _defines()
+    consts = {n: getattr(pkg, n) for n in dir(pkg) if n.startswith("SPH_") and isinstance(getattr(pkg, n), int)}
+    assert {"SPH_PREC_FP64", "SPH_PREC_MIXED", "SPH_LINES_THOMAS", "SPH_LINES_PARTITIONED",
+            "SPH_LINES_PARTITIONED_WARP"} <= set(consts)
+    for n, v in consts.items():
+        assert n in d and d[n] == v, (n, v, d.get(n))
+    names = ["avg", "coef", "rhs", "sweep_r", "sweep_theta", "sweep_phi"]
+    keys = ["SPH_K_AVG", "SPH_K_COEF", "SPH_K_RHS", "SPH_K_SWEEP_R", "SPH_K_SWEEP_TH", "SPH_K_SWEEP_PH"]
+    assert [pkg.Solver.KERNELS[d[k]] for k in keys] == names
+    # Solver.profile_read passes buffers of 8 entries
+    assert d["SPH_NKERNELS"] == 8 and len(pkg.Solver.KERNELS) <= d["SPH_NKERNELS"]
