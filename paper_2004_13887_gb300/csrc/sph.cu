@@ -1427,8 +1427,11 @@ static void line_layout(const Geo<double>& g, int d, SweepArgs<R>& S) {
 // inside a CUDA graph capture).
 template <int D, int P, int L, int CB>
 static int lines_attr() {
-  static int done = 0;
-  if (done) return SPH_OK;
+  static unsigned long long done = 0;  // one bit per device (attributes are per device)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPH_ERR_CUDA;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (done & bit) return SPH_OK;
   const int smb = lines::NFB * lines::Shape<P, L, CB>::FS * (int)sizeof(float);
   const int sms = lines::NFS * lines::Shape<P, L, CB>::FS * (int)sizeof(float);
   if (cudaFuncSetAttribute(lines::k_lines_blk<D, P, L, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb) !=
@@ -1436,7 +1439,7 @@ static int lines_attr() {
       cudaFuncSetAttribute(lines::k_lines_sca<D, P, L, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms) !=
           cudaSuccess)
     return SPH_ERR_CUDA;
-  done = 1;
+  done |= bit;
   return SPH_OK;
 }
 

@@ -50,7 +50,8 @@ constexpr int NR3 = 21;       // a normalised reduced row: A (0-8), C (9-17), r 
 constexpr unsigned FULL = 0xffffffffu;
 
 // per-lane floats of a block-line factor slot: (E, g, H) per interior cell
-__host__ __device__ constexpr int slot_floats(int P) { return (P > 1 ? P - 1 : 1) * NFAC; }
+// (none for chunks of one cell, which have no interior)
+__host__ __device__ constexpr int slot_floats(int P) { return (P > 1 ? P - 1 : 0) * NFAC; }
 
 // Shape of a launch: lines of n = L P cells, L lanes per line (16 or 32, or
 // 64 and 128 for lines spanning 2 and 4 warps), P cells per lane; a block
