@@ -36,11 +36,29 @@ WORKLOAD = ("rising thermal bubble, regional sector r=[6371,6381] km x 20 km x 2
 METRIC = "grid-point updates/s"
 UNIT = "points/s"
 
-# FP64 operations (DADD + DMUL + 2 DFMA, counted from the kernel's SASS
-# instruction mix with ncu) per line point of each kernel; None = not measured.
-FP64_FLOP_PER_POINT = {"rhs": 1103.2, "coef": 121.4, "sweep": 471.6}
-FP64_PEAK_TFLOPS = 1.257  # measured FP64 FMA throughput on the machine's GB300 (152 SMs x 2 FMA/clk x 2 x 2.07 GHz)
-HBM_PEAK_GBS = 6780.4     # measured copy bandwidth of the GB300s
+# FP64 operations (DADD + DMUL + 2 DFMA, counted from the kernels' SASS
+# instruction mix with ncu, profiles/fp64_counts_bubble_64cubed.md) per grid
+# point of one K = 2 step of the FP64 mode: 2 x (911 right-hand side + 158
+# coefficients + 1381 sweeps) + 15 (the second iteration's average).
+FP64_FLOP_PER_POINT_STEP = 4915.0
+# FP64 FMA throughput of GB300 measured on this machine with independent FMA
+# chains (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz); MEASURED_PEAKS.json has no
+# FP64 figure, so this is the library's own measurement.
+FP64_PEAK_TFLOPS = 1.257
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth in MEASURED_PEAKS.json, else
+    the profiling recipe's fallback figure"""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = hbm_peak()
 
 # Algorithmic bytes per grid point of each mixed-precision kernel launch: the
 # information it must move once -- no coefficient planes, no elimination
@@ -140,13 +158,13 @@ class ClockSampler:
 
 def oracle_grid(steps: int):
     """The oracle's sample of the workload for a run of `steps` steps: the whole
-    128 x 256 x 256 sector while that stays near a minute of host time (about
-    3 s per step on 16 cores), else its central 128 x w x w columns (same
-    cells, same bubble)."""
+    128 x 256 x 256 sector up to 60 steps (about 3 s per step on the GPU host's
+    16 cores, so the default 20 + 3 steps take about a minute), else its
+    central 128 x w x w columns (same cells, same bubble)."""
     from inputs import cases
-    if steps <= 20:
+    if steps <= 60:
         return cases.bubble_grid(GRID)
-    w = 128 if steps <= 80 else 64
+    w = 128 if steps <= 240 else 64
     return cases.bubble_window(GRID, (w, w))
 
 
@@ -193,7 +211,10 @@ def job_throughput(points_per_rank, steps, world, t_max_ms):
 
 
 def time_path(solver, args, dist, local):
-    """warm-up, then the timed steps (CUDA events on the library's stream)"""
+    """warm-up, then the timed steps (CUDA events on the library's stream, no
+    per-stage timing inside the timed region), then a separate pass of the
+    same number of steps with the library's per-stage CUDA events on, for the
+    stage shares and the dominant stage's launch time"""
     import torch
     for _ in range(args.warmup):
         solver.step(DT, K_ITER)
@@ -206,19 +227,22 @@ def time_path(solver, args, dist, local):
     torch.cuda.synchronize()
     sampler.start()
     l0 = solver.launches
-    solver.profile(True)
     e0.record(solver.stream)
     for _ in range(args.steps):
         solver.step(DT, K_ITER)
     e1.record(solver.stream)
     torch.cuda.synchronize()
-    kern = solver.profile_read()
-    solver.profile(False)
     launches = solver.launches - l0
     clocks = sampler.stop()
     if dist is not None:
         dist.barrier()
     t_max = max_over_ranks(e0.elapsed_time(e1), dist)
+    # stage profile: a separate pass (its events would perturb the headline)
+    solver.profile(True)
+    for _ in range(max(2, min(args.steps, 10))):
+        solver.step(DT, K_ITER)
+    kern = solver.profile_read()
+    solver.profile(False)
     return t_max, kern, launches, clocks
 
 
@@ -286,9 +310,17 @@ def run_ours(args, rank, world, dist):
     errors, fp64 = None, None
     if U64 is not None:
         errors = {"metric": "relative L2 after warmup+steps steps", **field_errors(Um, U64, c)}
+        ach64 = FP64_FLOP_PER_POINT_STEP * N * args.steps / (t64 * 1e-3) / 1e12
         fp64 = {"value": job_throughput(N, args.steps, world, t64), "ms_per_step": t64 / args.steps,
                 "kernel_shares": {k: round(v[0] / max(sum(x[0] for x in kern64.values()), 1e-30), 4)
-                                  for k, v in kern64.items() if v[1]}}
+                                  for k, v in kern64.items() if v[1]},
+                "roofline": {"bound": "fp64", "kernel": "whole FP64 step (all stages)", "unit": "TFLOP/s",
+                             "flop_per_point_step": FP64_FLOP_PER_POINT_STEP, "achieved": ach64,
+                             "peak": FP64_PEAK_TFLOPS, "frac": ach64 / FP64_PEAK_TFLOPS,
+                             "peak_source": "FP64 FMA rate measured by this library on the pool's GB300 "
+                                            "(MEASURED_PEAKS.json has no FP64 figure)",
+                             "hbm_note": "the FP64 step does ~4900 FP64 flop per point against ~1 KB of traffic: "
+                                         "bound by the FP64 pipe, not HBM"}}
 
     # dominant kernel of the mixed step and its HBM roofline
     dom = max(kern, key=lambda k: kern[k][0])
@@ -299,7 +331,7 @@ def run_ours(args, rank, world, dist):
     if dom in MEASURED_TRAFFIC and TRAFFIC_SOURCE_HASH == kernel_source_hash() and tuple(GRID) == TRAFFIC_GRID:
         traffic = MEASURED_TRAFFIC[dom] * N   # bytes per stage launch
     roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "peak": HBM_PEAK_GBS,
-            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "peak_source": HBM_PEAK_SOURCE, "timing": "CUDA events around each stage, separate pass of the same steps",
             "launch_ms": per_launch_ms, "traffic": traffic, "bytes_per_point": bpp}
     if bpp:
         achieved = bpp * N / (per_launch_ms * 1e-3) / 1e9
@@ -378,7 +410,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(GRID), "K": K_ITER, "dt_s": DT, "precision": "fp64",
-                       "sample_grid": [grid.nr, grid.nt, grid.np]},
+                       "sample_grid": [grid.nr, grid.nt, grid.np],
+                       "same_config": [grid.nr, grid.nt, grid.np] == list(GRID)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -71,7 +71,10 @@ size_t sph_field_size(const sph_grid* grid, int f);
  * legacy default stream).  The context owns all device buffers (state U^n,
  * iterate U^{n+1,k}, coefficients, right-hand sides, line-solve scratch).
  * Errors: SPH_ERR_ARG (nr, nth, nph < 2; r1 <= 0; empty ranges; periodic with
- * nph < 3), SPH_ERR_NOMEM, SPH_ERR_CUDA. */
+ * nph < 3; a grid too large for the kernels' 32-bit indexing: every field and
+ * the line-solve scratch, 18 values per cell (27 with periodic phi), must stay
+ * below 2^31 elements, i.e. at most about 1.19e8 cells on walled grids and
+ * 7.9e7 with periodic phi), SPH_ERR_NOMEM, SPH_ERR_CUDA. */
 int sph_create(const sph_grid* grid, const sph_params* params, void* stream, sph_ctx** out);
 
 /* Radial background (Section 3.2 hydrostatic state, or a constant): host arrays

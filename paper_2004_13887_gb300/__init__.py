@@ -116,19 +116,37 @@ def block_thomas_noalloc(A, B, Cb, d, stream=None):
     """Solve nlines independent 3x3-block tridiagonal lines without any device
     allocation inside the library (sph_block_thomas_noalloc).
 
-    A, B, Cb: CUDA float64 tensors (nlines, n, 3, 3); d: (nlines, n, 3).  The
-    output tensor is allocated here by torch, by the caller's side."""
+    A, B, Cb: CUDA float64 tensors (nlines, n, 3, 3); d: (nlines, n, 3), all on
+    one device.  The solve runs on that device, on `stream` (default: that
+    device's current stream).  The output tensor is allocated here by torch, on
+    the caller's side, in the stream the solve runs on.  Shapes, dtypes and
+    devices are checked before anything reaches the library (a smaller array
+    would be read past its end)."""
     import torch
-    nlines, n = int(B.shape[0]), int(B.shape[1])
     for t in (A, B, Cb, d):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-            raise TypeError("A, B, C, d must be contiguous CUDA float64 tensors")
-    x = torch.empty((nlines, n, 3), dtype=torch.float64, device=B.device)
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("A, B, C, d must be torch tensors")
+    if B.dim() != 4 or tuple(B.shape[2:]) != (3, 3):
+        raise ValueError(f"B must have shape (nlines, n, 3, 3), not {tuple(B.shape)}")
+    nlines, n = int(B.shape[0]), int(B.shape[1])
+    for name, t, shape in (("A", A, (nlines, n, 3, 3)), ("C", Cb, (nlines, n, 3, 3)), ("d", d, (nlines, n, 3))):
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, not {tuple(t.shape)}")
+    for t in (A, B, Cb, d):
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise TypeError("A, B, C, d must be contiguous float64 tensors")
+    if not all(t.is_cuda for t in (A, B, Cb, d)) or len({t.device for t in (A, B, Cb, d)}) != 1:
+        raise ValueError("A, B, C, d must be CUDA tensors on one device")
+    dev = B.device
     if stream is None:
-        stream = torch.cuda.current_stream()
-    p = [C.cast(C.c_void_p(t.data_ptr()), _DP) for t in (A, B, Cb, d, x)]
-    _check(load().sph_block_thomas_noalloc(nlines, n, *p, C.c_void_p(stream.cuda_stream)),
-           "sph_block_thomas_noalloc")
+        stream = torch.cuda.current_stream(dev)
+    elif stream.device != dev:
+        raise ValueError(f"stream is on {stream.device}, the tensors on {dev}")
+    with torch.cuda.device(dev), torch.cuda.stream(stream):
+        x = torch.empty((nlines, n, 3), dtype=torch.float64, device=dev)
+        p = [C.cast(C.c_void_p(t.data_ptr()), _DP) for t in (A, B, Cb, d, x)]
+        _check(load().sph_block_thomas_noalloc(nlines, n, *p, C.c_void_p(stream.cuda_stream)),
+               "sph_block_thomas_noalloc")
     return x
 
 

@@ -87,3 +87,27 @@ def test_binding_constants_match_header():
     assert [pkg.Solver.KERNELS[d[k]] for k in keys] == names
     # Solver.profile_read passes buffers of 8 entries
     assert d["SPH_NKERNELS"] == 8 and len(pkg.Solver.KERNELS) <= d["SPH_NKERNELS"]
+
+
+def test_noalloc_binding_checks_shapes_before_the_library(monkeypatch):
+    """block_thomas_noalloc rejects mismatched shapes, dtypes and devices before
+    it loads or calls the library (a smaller A, C or d would be read past its
+    end on the device)."""
+    import torch
+    import paper_2004_13887_gb300 as pkg
+
+    def boom(*a, **k):
+        raise AssertionError("the library must not be reached")
+    monkeypatch.setattr(pkg, "load", boom)
+    blk = lambda *s: torch.zeros(*s, dtype=torch.float64)
+    good = (blk(4, 6, 3, 3), blk(4, 6, 3, 3), blk(4, 6, 3, 3), blk(4, 6, 3))
+    for bad in ((blk(3, 6, 3, 3),) + good[1:],                      # fewer lines in A
+                good[:2] + (blk(4, 5, 3, 3), good[3]),             # shorter C
+                good[:3] + (blk(4, 6, 2),),                         # d's trailing dim
+                good[:1] + (blk(4, 6, 9),) + good[2:]):             # B not 3x3 blocks
+        with pytest.raises(ValueError):
+            pkg.block_thomas_noalloc(*bad)
+    with pytest.raises(TypeError):
+        pkg.block_thomas_noalloc(good[0].float(), *good[1:])
+    with pytest.raises(ValueError):   # host tensors: not CUDA
+        pkg.block_thomas_noalloc(*good)
