@@ -73,28 +73,47 @@ def test_tab_inc_low_mach_pressure_fluctuations():
                 assert got[n] <= 4.0 * printed and got[n] < 1e-3 * M0, (M0, n, got[n], printed)
 
 
+def _tcr_table():
+    """Tables tab:timept / tab:timeu (tests/golden/tab_tcr.txt): (field, tau, M0) -> printed TCR"""
+    out = {}
+    for row in _load("tab_tcr.txt"):
+        for M0, v in zip((1e-2, 1e-4, 1e-6), row[2:5]):
+            out[(row[0], float(row[1]), M0)] = float(v)
+    return out
+
+
 def test_time_convergence_rates():
-    """TCR at least the printed minimum 1.4 at tau = 1e-3 and 5e-4; at the smallest
-    tau every field inside the printed range [1.4, 3.3] and the mean close to 2.
-    (At tau = 1e-3 the velocity rate can exceed the printed maximum: the error is
-    still pre-asymptotic and falls faster than second order.)"""
+    """TCR(tau) = log2(|u^tau - u^{tau/2}| / |u^{tau/2} - u^{tau/4}|) at the printed
+    tau in {2e-3, 1e-3, 5e-4}, against Tables tab:timept and tab:timeu
+    (tests/golden/tab_tcr.txt; the paper's grid is not stated, so the rates are
+    compared, not matched digit by digit):
+    * every rate at least the smallest printed for that M0 less 0.3 (the printed
+      rates scatter from 1.4 to 3.2 around second order);
+    * at the smallest printed tau, 5e-4, the mean over the five fields within
+      0.3 of the printed mean, and no field above the largest printed rate of
+      that M0 plus 0.5.
+    (At tau = 2e-3 and 1e-3 the velocity rates at low Mach number can exceed the
+    printed maximum: the error there is pre-asymptotic and falls faster than
+    second order.)"""
     tend = 0.01
+    table = _tcr_table()
     fields = ["p", "ur", "ut", "up", "T"]
     for M0 in (1e-2, 1e-6):
         sols = {}
-        for tau in (1e-3, 5e-4, 2.5e-4, 1.25e-4):
+        for tau in (2e-3, 1e-3, 5e-4, 2.5e-4, 1.25e-4):
             U, _, _ = _run_paper_mms(M0, (8, 8, 24), int(round(tend / tau)), tau=tau)
             sols[tau] = U
-        for tau in (1e-3, 5e-4):
+        printed_all = [v for (f, t, m), v in table.items() if m == M0]
+        for tau in (2e-3, 1e-3, 5e-4):
             t2, t4 = tau / 2, tau / 4
-            tcr = [math.log2(np.linalg.norm(sols[tau][q] - sols[t2][q]) / np.linalg.norm(sols[t2][q] - sols[t4][q]))
-                   for q in range(5)]
-            for f, v in zip(fields, tcr):
-                assert v >= 1.4, (M0, tau, f, v)
-                if tau == 5e-4:
-                    assert v <= 3.3, (M0, tau, f, v)
+            tcr = {f: math.log2(np.linalg.norm(sols[tau][q] - sols[t2][q]) / np.linalg.norm(sols[t2][q] - sols[t4][q]))
+                   for q, f in enumerate(fields)}
+            for f, v in tcr.items():
+                assert v >= min(printed_all) - 0.3, (M0, tau, f, v)
             if tau == 5e-4:
-                assert 1.8 <= np.mean(tcr) <= 2.3, (M0, tcr)
+                printed = [table[(f, tau, M0)] for f in fields]
+                assert abs(np.mean(list(tcr.values())) - np.mean(printed)) <= 0.3, (M0, tcr, printed)
+                assert max(tcr.values()) <= max(printed_all) + 0.5, (M0, tcr)
 
 
 def test_space_convergence_sector_mms():
@@ -125,3 +144,47 @@ def test_space_convergence_paper_mms():
     errs = np.array(errs)
     rates = np.log2(errs[:-1] / errs[1:])
     assert np.all(rates[-1] > 1.7), (errs, rates)
+
+
+@pytest.mark.parametrize("M0", [1e-4, 1e-6])
+def test_space_convergence_paper_mms_low_mach(M0):
+    """Second-order l2 error in space at M0 = 1e-4 and 1e-6 as well (fig:conv,
+    tau = 2e-5 instead of the paper's 1e-5 to halve the run, t = 1e-3): the pressure rate approaches 2
+    from below (1.4 between the two coarser grids, 1.8 between the finer ones);
+    at M0 = 1e-6 the u_phi error is at the round-off level (the paper notes the
+    same), so it is bounded instead of rated."""
+    tau, steps = 2e-5, 50
+    errs = []
+    for n in ((16, 16, 48), (32, 32, 96)):
+        U, _, c = _run_paper_mms(M0, n, steps, tau=tau)
+        ex = c.exact(steps * tau)
+        errs.append([np.sqrt(np.mean((U[q] - ex[q]) ** 2)) for q in (0, 3)])
+    errs = np.array(errs)
+    rates = np.log2(errs[0] / errs[1])
+    assert rates[0] > 1.7, (errs, rates)
+    if M0 >= 1e-4:
+        assert rates[1] > 1.9, (errs, rates)
+    else:
+        assert errs[1, 1] < 1e-12, errs
+
+
+def test_tab_inc_at_the_paper_grid_diameter():
+    """Table tab:inc's grid diameter, 0.12 (max cell diagonal in physical space,
+    reading R13): 14 x 45 x 135 cells, diameter 0.122, one step of tau = 1e-3.
+    * M0 = 1e-2 reproduces the printed 3.2e-4 within 3 %.
+    * At M0 = 1e-6 the fluctuation with K = 2 carries an O(M0) part (7.6e-10,
+      against the printed 3.9e-12): the unconverged splitting iteration at an
+      acoustic Courant number c0 tau / h of about 3 on this grid (0.7 on the
+      16 x 11 x 33 grid of the test above).  K = 6 removes more than 90 % of it,
+      which pins the cause: the iteration, not the operators."""
+    n = (14, 45, 135)
+    got = {}
+    for M0, K in ((1e-2, 2), (1e-6, 2), (1e-6, 6)):
+        c = cases.paper_mms(M0, n=n)
+        U, _ = oracle.step(c.grid, c.par, c.init, 1e-3, K, bg=c.bg, walls_n=c.walls(0.0), walls_np1=c.walls(1e-3),
+                           S=c.source(0.5e-3))
+        got[(M0, K)] = np.max(np.abs(U[0])) / c.info["p0"]
+    rows = {int(r[0]): list(map(float, r[1:])) for r in _load("tab_inc.txt")}
+    assert abs(got[(1e-2, 2)] - rows[1][0]) <= 0.03 * rows[1][0], got
+    assert got[(1e-6, 2)] > 10 * rows[1][4], got                 # the O(M0) splitting part is there
+    assert got[(1e-6, 6)] < 0.1 * got[(1e-6, 2)], got            # and it is the iteration's

@@ -171,3 +171,57 @@ def test_periodic_shift_equivariance():
     C, _ = oracle.step(g, par, V, 0.01, 2)
     for q in range(5):
         assert np.max(np.abs(C[q] - C[q][:, :, :1])) <= 1e-12 * (np.max(np.abs(C[q])) + 1e-300)
+
+
+def _closed_box_flow(n):
+    """A sourceless flow in a closed sector: no-slip walls with zero normal
+    velocity, smooth velocity and pressure perturbations (paper's constants of
+    Section 3.1, mu = 0.05)."""
+    from inputs import Grid, Params
+    par = Params(gamma=1.6, cv=1.0, Pr=1.0, mu=0.05)
+    p0 = 6250.0
+    T0 = p0 / (par.cv * (par.gamma - 1))
+    g = Grid(n, n, n, 1.0, 2.0, np.pi / 4, 3 * np.pi / 4, np.pi / 4, 7 * np.pi / 4)
+    U = g.zeros()
+    for f in (1, 2, 3):
+        R, TH, PH = g.coords(f)
+        xi, et, ze = (R - g.r1) / (g.r2 - g.r1), (TH - g.t1) / (g.t2 - g.t1), (PH - g.p1) / (g.p2 - g.p1)
+        U[f][:] = 5.0 * np.sin(np.pi * xi) * np.sin(np.pi * et) * np.sin(np.pi * ze) * (
+            1 + 0.5 * np.cos(2 * np.pi * (xi + 0.3 * f)) * np.sin(np.pi * (et + ze)))
+    U[1][0] = U[1][-1] = 0
+    U[2][:, 0] = U[2][:, -1] = 0
+    U[3][:, :, 0] = U[3][:, :, -1] = 0
+    R, TH, PH = g.coords(0)
+    xi, et, ze = (R - g.r1) / (g.r2 - g.r1), (TH - g.t1) / (g.t2 - g.t1), (PH - g.p1) / (g.p2 - g.p1)
+    U[0][:] = 20 * np.cos(np.pi * xi) * np.cos(np.pi * et) * np.cos(np.pi * ze)
+    bg = (np.full(n + 2, p0), np.full(n + 2, T0))
+    return g, par, bg, U, p0, T0
+
+
+def _mass(g, par, U, p0, T0):
+    """sum of rho (eq. nonconserveos) times the exact cell volumes"""
+    rf, tf = g.rf(), g.tf()
+    V = ((rf[1:] ** 3 - rf[:-1] ** 3) / 3)[:, None, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :, None] * g.dph
+    rho = (p0 + U[0]) / (par.cv * (par.gamma - 1) * (T0 + U[4]))
+    return float(np.sum(rho * V))
+
+
+def test_mass_drift_falls_at_second_order():
+    """The scheme evolves p and T, not rho (the T-equation replaces the mass
+    equation, Section 2.1 and Appendix A), so the total mass of a closed,
+    sourceless flow -- exactly conserved by the continuous problem -- is not a
+    discrete invariant: it drifts, and the drift is a discretisation error that
+    falls at second order under refinement (tau small enough that the O(tau^2)
+    part does not mask it)."""
+    tau, steps = 1.25e-4, 80
+    drift = []
+    for n in (8, 16, 32):
+        g, par, bg, U, p0, T0 = _closed_box_flow(n)
+        m0 = _mass(g, par, U, p0, T0)
+        for _ in range(steps):
+            U, _ = oracle.step(g, par, U, tau, 2, bg=bg)
+        drift.append(abs(_mass(g, par, U, p0, T0) - m0) / m0)
+    drift = np.array(drift)
+    rates = np.log2(drift[:-1] / drift[1:])
+    assert drift[0] > 1e-8, drift           # not conserved to round-off: a non-conservative scheme
+    assert np.all(rates >= 1.8), (drift, rates)
