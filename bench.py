@@ -473,6 +473,80 @@ def run_ensemble(args, rank, world, dist):
     return line
 
 
+def run_adjoint(args, rank, world, dist):
+    """The gradient workload: d(final kinetic energy)/d(initial potential-
+    temperature perturbation) over 20 steps of a 96 x 192 x 192 bubble (plus 1e-3
+    white noise), FP64, through the autograd Function with checkpoints every
+    ceil(sqrt(20)) = 5 steps; the gradient checked against central differences
+    along 2 seeded directions.  Metric: grid-point updates/s of the forward
+    steps, the adjoint steps and the recomputation together."""
+    import numpy as np
+    import torch
+    import paper_2004_13887_gb300 as sph
+    from paper_2004_13887_gb300 import adjoint
+    from inputs import cases
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        sph.build()
+    c = cases.adjoint_bubble()
+    g, par, bg = c.grid, c.par, c.bg
+    nsteps = 20
+    s = sph.Solver(g, par)
+    s.set_background(*bg)
+    Pi = torch.as_tensor(c.info["Pi"], device="cuda")
+    base = [torch.as_tensor(f, device="cuda") for f in c.init]
+    th0 = torch.as_tensor(c.info["theta0"], device="cuda")
+
+    def J_of(theta):
+        U0 = [base[0], base[1], base[2], base[3], Pi * theta]
+        return adjoint.kinetic_energy(adjoint.steps(s, c.dt, K_ITER, nsteps, U0), g, bg, par)
+
+    # warm-up (allocates the adjoint's workspace), then the timed gradient
+    th = th0.clone().requires_grad_(True)
+    J_of(th).backward()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = s.launches
+    t0 = time.perf_counter()
+    th = th0.clone().requires_grad_(True)
+    J = J_of(th)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    clocks = sampler.stop()
+    launches = s.launches - l0
+    grad = th.grad.detach()
+    rng = np.random.default_rng(7)
+    checks = []
+    with torch.no_grad():
+        for _ in range(2):
+            v = torch.as_tensor(rng.standard_normal(g.shapes()[4]), device="cuda")
+            eps = 1e-4
+            fd = (float(J_of(th0 + eps * v)) - float(J_of(th0 - eps * v))) / (2 * eps)
+            ad = float(torch.sum(grad * v))
+            checks.append(abs(fd - ad) / max(abs(fd), 1e-300))
+    longest, cap = s.tape_use()
+    s.close()
+    # forward 20 steps + backward (20 recomputed steps + 20 adjoint steps)
+    N = g.npoints
+    total = t2 - t0
+    line = {"metric": "grid-point updates/s of the gradient (forward + recompute + adjoint steps)",
+            "value": N * nsteps / total, "unit": UNIT, "n_gpus": world, "steps": nsteps, "warmup": 1,
+            "ms_per_step": 1e3 * total / nsteps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "adjoint: gradient of the final kinetic energy after 20 steps w.r.t. the initial "
+                                   "potential-temperature perturbation, bubble 96x192x192 + 1e-3 white noise, K=2, "
+                                   "dt=1 s, checkpoints every 5 steps", "grid": [g.nr, g.nt, g.np]},
+            "forward_s": t1 - t0, "backward_s": t2 - t1, "kinetic_energy": float(J),
+            "fd_check_rel_diff": checks, "tape_longest": longest, "tape_capacity": cap,
+            "gpu_launches": launches, "clocks": clocks}
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,8 +555,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", default=None, help="nr,nt,np of a smaller sector (profiling of small cases)")
-    ap.add_argument("--workload", choices=["bubble", "ensemble"], default="bubble",
-                    help="ensemble: the 64-instance batched ensemble instead of the benchmark workload")
+    ap.add_argument("--workload", choices=["bubble", "ensemble", "adjoint"], default="bubble",
+                    help="ensemble: the 64-instance batched ensemble; adjoint: the gradient workload "
+                         "(instead of the benchmark workload)")
     ap.add_argument("--only", choices=["both", "mixed", "fp64"], default="both",
                     help="profiling: run one path only (the JSON line then lacks the other)")
     args = ap.parse_args()
@@ -506,8 +581,8 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist_.init_process_group("nccl")
         dist = dist_
-    if args.workload == "ensemble":
-        line = run_ensemble(args, rank, world, dist)
+    if args.workload in ("ensemble", "adjoint"):
+        line = (run_ensemble if args.workload == "ensemble" else run_adjoint)(args, rank, world, dist)
         if rank == 0:
             print(json.dumps(line), flush=True)
         if dist is not None:

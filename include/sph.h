@@ -16,9 +16,11 @@
  *    elements:  p, T: nr*nt*np (centres); u_r: (nr+1)*nt*np (r-faces);
  *    u_theta: nr*(nt+1)*np (theta-faces); u_phi: nr*nt*npf (phi-faces) with
  *    npf = np+1, or np when phi is periodic.
- *  - Boundary conditions: u = 0 tangentially on every wall (no-slip; ghost =
- *    -interior), the normal velocity on wall faces is whatever the state holds
- *    there and is not changed by sph_step; zero normal derivative of p' and T';
+ *  - Boundary conditions: Dirichlet velocity on every wall -- by default u = 0
+ *    tangentially (no-slip; ghost = -interior) and the normal velocity on wall
+ *    faces is whatever the state holds there, unchanged by sph_step; wall data
+ *    that vary in time are set with sph_set_bc -- and zero normal derivative of
+ *    p' and T' (Section 3.1: zero Neumann for pressure and temperature);
  *    optional periodic phi (cyclic line systems).
  *  - Pointers marked "device" are CUDA device pointers of the current device;
  *    "host" pointers are ordinary host memory.  The library never keeps a
@@ -41,6 +43,7 @@ extern "C" {
 #define SPH_ERR_NONFINITE (-3)  /* NaN/Inf in the new state; the state is left at U^n */
 #define SPH_ERR_SINGULAR (-4)   /* a zero pivot in a line solve; state left at U^n */
 #define SPH_ERR_NOMEM (-5)      /* device allocation failed */
+#define SPH_ERR_TAPE (-6)       /* sph_step_adjoint: a per-thread tape was too short */
 
 #define SPH_PREC_FP64 0          /* every step in FP64 */
 #define SPH_PREC_MIXED 1         /* FP32 bulk stencils/line solves, FP64 iterate */
@@ -82,6 +85,28 @@ int sph_create(const sph_grid* grid, const sph_params* params, void* stream, sph
  * NULL sets that background to zero (the default). */
 int sph_set_background(sph_ctx* ctx, const double* p_ref, const double* T_ref);
 
+/* Dirichlet data for the velocity on the walls (Section 3.1: the
+ * manufactured-solution test imposes the exact, time-dependent velocity on
+ * every boundary; pressure and temperature keep zero normal derivatives).
+ * w_n, w_np1: arrays of 18 pointers (host or device per on_device) with the
+ * wall values at t^n and t^{n+1} of the coming steps; a NULL entry counts as
+ * zero, and w_n = w_np1 = NULL returns to homogeneous walls.  Entry
+ * (c*3 + d)*2 + s is velocity component c (0 r, 1 theta, 2 phi) on the wall
+ * normal to direction d (0 r, 1 theta, 2 phi) at side s (0 low, 1 high), C
+ * order with phi fastest over the wall's two other indices:
+ *   c = r:     d = r  nth*nph,   d = theta (nr+1)*nph, d = phi (nr+1)*nth
+ *   c = theta: d = r (nth+1)*nph, d = theta nr*nph,    d = phi nr*(nth+1)
+ *   c = phi:   d = r nth*npf,    d = theta nr*npf,     d = phi nr*nth
+ * (npf as for the u_phi field).  c != d: the tangential value w on the wall,
+ * used by the ghost rule ghost = 2 w - interior, taken at the midpoint level
+ * (w^n + w^{n+1})/2 with Ubar.  c == d: the normal velocity on the wall faces:
+ * each sph_step starts its iteration from U^{n+1,0} = U^n with these faces set
+ * to the t^{n+1} values (U^n keeps its own).  On a periodic phi line the d =
+ * phi entries are ignored.  The data stay in effect for every later step until
+ * the next call (a caller with moving walls calls it before each step).
+ * Synchronises the context's stream.  Errors: SPH_ERR_NOMEM, SPH_ERR_CUDA. */
+int sph_set_bc(sph_ctx* ctx, const double* const* w_n, const double* const* w_np1, int on_device);
+
 /* Copy the 5 fields in (host or device per on_device) into U^n. */
 int sph_set_state(sph_ctx* ctx, const double* const* fields, int on_device);
 
@@ -107,6 +132,29 @@ int sph_step(sph_ctx* ctx, double dt, int n_iter, const double* const* source, i
  * sph_step itself clears pending flags. */
 int sph_step_async(sph_ctx* ctx, double dt, int n_iter, const double* const* source, int source_on_device);
 int sph_status(sph_ctx* ctx, double* residual_out);
+
+/* Adjoint of one step (the reverse mode of the map U^n -> U^{n+1} that sph_step
+ * computes: Section 2.2's K Picard iterations of eq. splitting2, each a
+ * right-hand side (eq. spl1) and the sweeps spl1-spl3 with every coefficient
+ * frozen at Ubar = (U^{n+1,k} + U^n)/2, eq. chapter3mainsd).  FP64 contexts only
+ * (SPH_ERR_ARG otherwise).  The context's U^n is the step's input state; it is
+ * not changed.  lam_out: 5 device arrays, dJ/dU^{n+1} of a functional J;
+ * lam_in: 5 device arrays that receive dJ/dU^n (both in the field layout of
+ * sph_set_state; may not alias).  source: NULL or the 5 device arrays the step
+ * was given.  Wall data set by sph_set_bc are constants of the step.  The call
+ * recomputes the step's iterates, then runs the iterations backwards: per
+ * iteration the transposed line solves (phi, theta, r) and the gradient over
+ * Ubar of the right-hand side and of the three line operators, by reverse-mode
+ * differentiation of the library's own row functions.  Work buffers (about 16
+ * fields plus 17 coefficient planes and the per-thread tapes, ~2 GB) are
+ * allocated on the first call and kept with the context.  Synchronises.
+ * Errors: SPH_ERR_ARG, SPH_ERR_NOMEM, SPH_ERR_CUDA, SPH_ERR_SINGULAR (a zero pivot
+ * in a transposed solve), SPH_ERR_TAPE (a location's rows outgrew the tape). */
+int sph_step_adjoint(sph_ctx* ctx, double dt, int n_iter, const double* const* source,
+                     const double* const* lam_out, double* const* lam_in);
+/* The longest per-thread tape the adjoint has used so far and the capacity
+ * (synchronises). */
+int sph_adjoint_tape_use(sph_ctx* ctx, int* longest, int* capacity);
 
 /* Batches of independent contexts (an ensemble of problems, e.g. of different
  * grid sizes) stepped by one CUDA graph.  sph_batch_create: n distinct contexts

@@ -276,6 +276,25 @@ def thermal2(n=(200, 200, 200), dt: float = 1.0, K: int = 2) -> Case:
     return c
 
 
+ADJOINT_SEED = 4
+
+
+def adjoint_bubble(n=(96, 192, 192), seed: int = ADJOINT_SEED, dt: float = 1.0, noise: float = 1e-3) -> Case:
+    """The gradient workload: a Gaussian bubble (the benchmark's, seeded) on a
+    96 x 192 x 192 sector plus white noise of 1e-3 K on the potential-temperature
+    perturbation; 20 steps.  info: theta0 (the perturbation, cell centres) and
+    Pi (the background Exner function at the centres, T' = Pi theta')."""
+    c = bubble(n, seed=seed, dt=dt, steps=20)
+    bgT = c.bg[1]
+    Pi = (bgT[1:-1] / 300.0)[:, None, None]
+    rng = np.random.default_rng(seed + 1000)
+    theta0 = c.init[4] / Pi + noise * rng.standard_normal(c.grid.shapes()[4])
+    c.init[4] = np.ascontiguousarray(Pi * theta0)
+    c.info.update(theta0=theta0, Pi=np.ascontiguousarray(np.broadcast_to(Pi, c.grid.shapes()[4])))
+    c.name = "adjoint_bubble"
+    return c
+
+
 ENSEMBLE_SEED = 20041389
 
 

@@ -26,7 +26,7 @@ SPH_LINES_PARTITIONED = 1
 SPH_LINES_PARTITIONED_WARP = 2
 
 _ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "non-finite state",
-           -4: "zero pivot in a line solve", -5: "device allocation failed"}
+           -4: "zero pivot in a line solve", -5: "device allocation failed", -6: "adjoint tape too short"}
 
 
 class SphError(RuntimeError):
@@ -56,6 +56,7 @@ SIGNATURES = {
     "sph_field_size": ([C.POINTER(sph_grid), C.c_int], C.c_size_t),
     "sph_create": ([C.POINTER(sph_grid), C.POINTER(sph_params), C.c_void_p, C.POINTER(_CTX)], C.c_int),
     "sph_set_background": ([_CTX, _DP, _DP], C.c_int),
+    "sph_set_bc": ([_CTX, _PP, _PP, C.c_int], C.c_int),
     "sph_set_state": ([_CTX, _PP, C.c_int], C.c_int),
     "sph_get_state": ([_CTX, _PP, C.c_int], C.c_int),
     "sph_step": ([_CTX, C.c_double, C.c_int, _PP, C.c_int, _DP], C.c_int),
@@ -75,6 +76,8 @@ SIGNATURES = {
     "sph_profile_read": ([_CTX, _DP, C.POINTER(C.c_longlong)], C.c_int),
     "sph_destroy": ([_CTX], None),
     "sph_block_thomas_noalloc": ([C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP, C.c_void_p], C.c_int),
+    "sph_step_adjoint": ([_CTX, C.c_double, C.c_int, _PP, _PP, _PP], C.c_int),
+    "sph_adjoint_tape_use": ([_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "sph_strerror": ([C.c_int], C.c_char_p),
 }
 
@@ -216,6 +219,48 @@ class Solver:
         _check(load().sph_set_background(self._h, a.ctypes.data_as(_DP) if a is not None else None,
                                          b.ctypes.data_as(_DP) if b is not None else None), "sph_set_background")
 
+    def set_bc(self, walls_n=None, walls_np1=None):
+        """Dirichlet wall velocity at t^n and t^{n+1} for the coming steps
+        (sph_set_bc).  walls_*: None or a dict {(c, d, s): array} -- component
+        c on the wall normal to direction d at side s -- of numpy arrays (or
+        CUDA float64 tensors) in the header's layout; both None = homogeneous
+        walls."""
+        if walls_n is None and walls_np1 is None:
+            _check(load().sph_set_bc(self._h, None, None, 0), "sph_set_bc")
+            return
+        g = self.grid
+        sizes = {}
+        for c in range(3):
+            for d in range(3):
+                sizes[(c, d)] = int(np.prod(g.wall_shape(c, d)))
+        keep = []
+        dev = None
+        arrs = []
+        for walls in (walls_n, walls_np1):
+            ptrs = [None] * 18
+            for (c, d, s), a in (walls or {}).items():
+                is_dev = not isinstance(a, np.ndarray)
+                if dev is None:
+                    dev = is_dev
+                elif dev != is_dev:
+                    raise ValueError("wall arrays must all be host arrays or all CUDA tensors")
+                if is_dev:
+                    if not (a.is_cuda and a.dtype == torch_float64()):
+                        raise TypeError("device wall data must be CUDA float64 tensors")
+                    a = a.contiguous()
+                    ptr = C.cast(C.c_void_p(a.data_ptr()), _DP)
+                    n = a.numel()
+                else:
+                    a = np.ascontiguousarray(a, dtype=np.float64)
+                    ptr = a.ctypes.data_as(_DP)
+                    n = a.size
+                if n != sizes[(c, d)]:
+                    raise ValueError(f"wall array {(c, d, s)} has {n} values, needs {sizes[(c, d)]}")
+                keep.append(a)
+                ptrs[(c * 3 + d) * 2 + s] = ptr
+            arrs.append((_DP * 18)(*ptrs))
+        _check(load().sph_set_bc(self._h, arrs[0], arrs[1], int(bool(dev))), "sph_set_bc")
+
     def set_state(self, fields):
         dev = not isinstance(fields[0], np.ndarray)
         p = _Ptrs(fields, self.shapes, dev)
@@ -276,6 +321,26 @@ class Solver:
         res = np.zeros(5) if residual else None
         _check(load().sph_status(self._h, res.ctypes.data_as(_DP) if res is not None else None), "sph_status")
         return res
+
+    # ------------------------------------------------------------ adjoint
+    def step_adjoint(self, dt: float, n_iter: int, lam_out, source=None):
+        """dJ/dU^n from dJ/dU^{n+1} for the step sph_step takes from the current
+        state U^n (sph_step_adjoint; FP64 solvers).  lam_out: 5 CUDA float64
+        tensors; source: the step's 5 device source arrays or None.  Returns 5
+        new CUDA tensors."""
+        lam_in = self.empty()
+        lo = _Ptrs(lam_out, self.shapes, True)
+        li = _Ptrs(lam_in, self.shapes, True)
+        src = _Ptrs(source, self.shapes, True) if source is not None else None
+        _check(load().sph_step_adjoint(self._h, float(dt), int(n_iter), src.arr if src else None, lo.arr, li.arr),
+               "sph_step_adjoint")
+        return lam_in
+
+    def tape_use(self):
+        """(longest per-thread tape used by the adjoint so far, capacity)"""
+        a, b = C.c_int(0), C.c_int(0)
+        _check(load().sph_adjoint_tape_use(self._h, C.byref(a), C.byref(b)), "sph_adjoint_tape_use")
+        return a.value, b.value
 
     # ------------------------------------------------------------- stages
     def rhs(self, dt: float, source=None):

@@ -128,10 +128,14 @@ __global__ void k_cvt_in(long n, const double* __restrict__ a, R* __restrict__ o
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += s) o[t] = (R)a[t];
 }
 
-template <bool CIJ, typename R>
-__device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<R>& ub, const Coef<R>& c, int i, int j,
+// The coefficients of centre (i, j, k) (flat index t) into c: the planes of a
+// Coef (k_coef), or the adjoint's slots for the same values.
+template <bool CIJ, typename R, typename Out>
+__device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<R>& ub, const Out& c, int i, int j,
                                         int k, int t) {
-  const R *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
+  const auto UR = ub.f[1];
+  const auto UT = ub.f[2];
+  const auto UP = ub.f[3];
   // thermodynamics from background + perturbation.  The density perturbation
   // rho - rho_ref = (p' T_ref - (p_ref + pi_inf) T') / (Rg T_ref T) has no
   // cancellation between large terms, so the bulk type keeps its relative
@@ -254,13 +258,35 @@ __device__ __forceinline__ float div_ubar_ff(const Geo<float>& g, const CF<float
   return sh + sl;
 }
 
-// R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per centre.
-template <bool CIJ, typename R>
+// div(Ubar) at centre (i,j,k) from Ubar itself (the adjoint's evaluation: the
+// FP64 kernels form it from U^n and U^k, the same value up to rounding)
+template <typename R>
+__device__ __forceinline__ R div_ubar_of(const Geo<R>& g, const CF<R>& ub, int i, int j, int k) {
+  int a0 = IRf(g, i, j, k), a1 = IRf(g, i + 1, j, k);
+  int b0 = ITf(g, i, j, k), b1 = ITf(g, i, j + 1, k);
+  int kp = g.per ? wrapk(g, k + 1) : k + 1;
+  int c0 = IPf(g, i, j, k), c1 = IPf(g, i, j, kp);
+  auto ir = g.irc[i], is = g.isc[j];
+  auto f0 = g.rf[i] * g.rf[i], f1 = g.rf[i + 1] * g.rf[i + 1];
+  R dr_ = (f1 * ub.f[1][a1] - f0 * ub.f[1][a0]) * (ir * ir * g.idr);
+  R dt_ = (g.sf[j + 1] * ub.f[2][b1] - g.sf[j] * ub.f[2][b0]) * (ir * is * g.idth);
+  R dp_ = (ub.f[3][c1] - ub.f[3][c0]) * (ir * is * g.idph);
+  return dr_ + dt_ + dp_;
+}
+
+// R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per
+// centre; written to Rout.f[0][t], Rout.f[4][t] (a field pair, or the adjoint's
+// slots).
+template <bool CIJ, typename R, typename Out>
 __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd, const Par& P, const Coef<R>& c,
                                          const CF<R>& ub, const CF<R>& ul, const CF<double>& un, const CF<double>& uk,
                                          const CF<R>& D, int hasD, const CF<double>& src, int has_src, R tau,
-                                         const MF<R>& Rout, int i, int j, int k, int t) {
-  const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3], *TT = ub.f[4];
+                                         const Out& Rout, int i, int j, int k, int t) {
+  const auto Pp = ub.f[0];
+  const auto UR = ub.f[1];
+  const auto UT = ub.f[2];
+  const auto UP = ub.f[3];
+  const auto TT = ub.f[4];
   R mu = pick<R>(P.mu, P.mu_f), gm = pick<R>(P.gamma, P.gamma_f);
   R ir = g.irc[i];
   R accp = R(0), accT = R(0);
@@ -289,8 +315,9 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
     aT = w.a;
   }
   R divu;
-  if constexpr (sizeof(R) == sizeof(double)) divu = div_ubar(gd, un, uk, i, j, k);
-  else divu = div_ubar_ff(g, ub, ul, i, j, k);
+  if constexpr (is_f32<R>) divu = div_ubar_ff(g, ub, ul, i, j, k);
+  else if constexpr (std::is_same<R, double>::value) divu = div_ubar(gd, un, uk, i, j, k);
+  else divu = div_ubar_of(g, ub, i, j, k);
   // Cross terms of the viscous dissipation: the centred derivative sums
   // d_r u_t + d_t u_r / r, d_r u_p + d_p u_r / (r sin), d_t u_p / r + d_p u_t / (r sin)
   // of the centre-averaged velocities.  k_coef forms the same sums minus the
@@ -324,12 +351,15 @@ __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_c(Geo<R> g, Geo<do
 }
 
 // R for the momentum row of component D on its faces: one thread per face
-// (zero on wall faces, which are not unknowns).
-template <bool CIJ, int D, typename R>
+// (zero on wall faces, which are not unknowns); written to Rout.f[1 + D][t].
+template <bool CIJ, int D, typename R, typename Out>
 __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub,
                                          const CF<R>& Dv, int hasD, const CF<double>& src, int has_src, R tau,
-                                         const MF<R>& Rout, int i, int j, int k, int t) {
-  const R *Pp = ub.f[0], *UR = ub.f[1], *UT = ub.f[2], *UP = ub.f[3];
+                                         const Out& Rout, int i, int j, int k, int t) {
+  const auto Pp = ub.f[0];
+  const auto UR = ub.f[1];
+  const auto UT = ub.f[2];
+  const auto UP = ub.f[3];
   R mu = pick<R>(P.mu, P.mu_f), om = pick<R>(P.omega, P.omega_f), h = R(0.5);
   R wp[2], wu[3], w[3];
   R acc;
@@ -547,28 +577,78 @@ struct SweepArgs {
   int* flag;
 };
 
+// Per-thread sums of squares of the increments, per field (the iteration
+// residual).  FP64 mode: plain FP64 sums.  FP32 mode: each sum is an
+// unevaluated pair hi + lo (the square's rounding error by FMA, the addition's
+// by two_sum), ~48 bits like an FP64 sum, on the FP32 pipe; the warp's pairs are
+// combined the same way and reach the FP64 accumulator as hi + lo.
+template <typename R>
+struct SqSum {
+  R h[5] = {0, 0, 0, 0, 0};
+  __device__ __forceinline__ void add(int f, R r) { h[f] += r * r; }
+  __device__ __forceinline__ double warp_total(int f) const {
+    R v = h[f];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return f2d(v);
+  }
+};
+template <>
+struct SqSum<float> {
+  float h[5] = {0, 0, 0, 0, 0}, l[5] = {0, 0, 0, 0, 0};
+  __device__ __forceinline__ void add(int f, float r) {
+    float p = r * r, e = fmaf(r, r, -p), s, t;
+    two_sum(h[f], p, s, t);
+    h[f] = s;
+    l[f] += t + e;
+  }
+  __device__ __forceinline__ double warp_total(int f) const {
+    float hv = h[f], lv = l[f];
+    for (int o = 16; o > 0; o >>= 1) {
+      float ho = __shfl_down_sync(0xffffffffu, hv, o), lo = __shfl_down_sync(0xffffffffu, lv, o), s, t;
+      two_sum(hv, ho, s, t);
+      hv = s;
+      lv += lo + t;
+    }
+    return f2d(hv) + f2d(lv);
+  }
+};
+// The same with plain FP32 partial sums per thread (a few squares each: the
+// scalar line kernels, whose 48-register budget has no room for the pairs) and
+// the pair combination from the warp reduction on.
+struct SqSumLite {
+  float h[5] = {0, 0, 0, 0, 0};
+  __device__ __forceinline__ void add(int f, float r) { h[f] = fmaf(r, r, h[f]); }
+  __device__ __forceinline__ double warp_total(int f) const {
+    float hv = h[f], lv = 0.f;
+    for (int o = 16; o > 0; o >>= 1) {
+      float ho = __shfl_down_sync(0xffffffffu, hv, o), lo = __shfl_down_sync(0xffffffffu, lv, o), s, t;
+      two_sum(hv, ho, s, t);
+      hv = s;
+      lv += lo + t;
+    }
+    return f2d(hv) + f2d(lv);
+  }
+};
+
 // store a value of field f at flat index idx: x (mode 0) or uk = base + v (mode
 // 1, the one FP64 add per value of the mixed path), with the square of v summed
-// in the bulk type
-template <typename R, typename V>
-__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, int idx, V v, R* ss, int* bad) {
+template <typename R, typename V, typename Acc>
+__device__ __forceinline__ void put(const SweepArgs<R>& A, int f, int idx, V v, Acc& ss, int* bad) {
   if (!A.update) {
     A.x.f[f][idx] = (R)v;
   } else {
     double nv = A.base.f[f][idx] + f2d(v);
     if (!isfinite(v)) *bad |= FLAG_NONFINITE;  // the state was finite; only a non-finite increment spoils it
     A.uk.f[f][idx] = nv;
-    R r = (R)v;
-    ss[f] += r * r;
+    ss.add(f, (R)v);
   }
 }
 // the update-mode store with the FP64 state value already loaded
-template <typename R, typename V>
-__device__ __forceinline__ void put_upd(const SweepArgs<R>& A, int f, int idx, double base, V v, R* ss, int* bad) {
+template <typename R, typename V, typename Acc>
+__device__ __forceinline__ void put_upd(const SweepArgs<R>& A, int f, int idx, double base, V v, Acc& ss, int* bad) {
   if (!isfinite(v)) *bad |= FLAG_NONFINITE;
   A.uk.f[f][idx] = base + f2d(v);
-  R r = (R)v;
-  ss[f] += r * r;
+  ss.add(f, (R)v);
 }
 // wall face of field f: x = 0, or uk = base (mode 1)
 template <typename R>
@@ -577,8 +657,46 @@ __device__ __forceinline__ void put_wall(const SweepArgs<R>& A, int f, int idx) 
   else A.uk.f[f][idx] = A.base.f[f][idx];
 }
 
-template <typename R, int D>
-__device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, R* ss, int* bad) {
+// Blocks of row m of the transposed line matrix: (M^T)_{m,m-1} = C_{m-1}^T,
+// (M^T)_{m,m} = B_m^T, (M^T)_{m,m+1} = A_{m+1}^T, wrapping on a cyclic line and
+// zero past the ends of a walled one (the adjoint's transposed line solves).
+template <typename R>
+__device__ __forceinline__ void transposed_blocks(const SweepArgs<R>& S, int d, int n, int cyc, int a, int b, int m,
+                                                  R* A, R* B, R* C) {
+  R X[9], Y[9], Z[9];
+  int i, j, k;
+  line_pos(d, a, b, m, i, j, k);
+  assemble_block(S.g, S.P, S.c, S.ub, d, n, cyc, m, i, j, k, S.h, X, Y, Z);
+#pragma unroll
+  for (int r = 0; r < 3; r++)
+#pragma unroll
+    for (int q = 0; q < 3; q++) B[r * 3 + q] = Y[q * 3 + r];
+  int mp = m - 1, mn = m + 1;
+  if (cyc) { mp = mp < 0 ? n - 1 : mp; mn = mn == n ? 0 : mn; }
+#pragma unroll
+  for (int q = 0; q < 9; q++) { A[q] = R(0); C[q] = R(0); }
+  if (mp >= 0) {
+    line_pos(d, a, b, mp, i, j, k);
+    assemble_block(S.g, S.P, S.c, S.ub, d, n, cyc, mp, i, j, k, S.h, X, Y, Z);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int q = 0; q < 3; q++) A[r * 3 + q] = Z[q * 3 + r];
+  }
+  if (mn < n) {
+    line_pos(d, a, b, mn, i, j, k);
+    assemble_block(S.g, S.P, S.c, S.ub, d, n, cyc, mn, i, j, k, S.h, X, Y, Z);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int q = 0; q < 3; q++) C[r * 3 + q] = X[q * 3 + r];
+  }
+}
+
+// One block line along D: solve (I + h D_D) x = rhs (TR: its transpose) by
+// block Thomas, Woodbury-corrected on a cyclic line.
+template <typename R, int D, bool TR = false>
+__device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, SqSum<R>& ss, int* bad) {
   const Geo<R>& g = S.g;
   constexpr int d = D;
   int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
@@ -593,7 +711,8 @@ __device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, R* ss,
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
     R A[9], B[9], C[9];
-    assemble_block(g, S.P, S.c, S.ub, d, n, cyc, m, i, j, k, S.h, A, B, C);
+    if constexpr (TR) transposed_blocks(S, d, n, cyc, a, b, m, A, B, C);
+    else assemble_block(g, S.P, S.c, S.ub, d, n, cyc, m, i, j, k, S.h, A, B, C);
     R rr[12];
     int ic = IC(g, i, j, k);
     rr[0] = S.rhs.f[0][ic];
@@ -752,14 +871,32 @@ __device__ __forceinline__ void scalar_walls(const SweepArgs<R>& S, int cc, int 
 
 // output of a transverse line value at cell m, plus the wall faces of that
 // component next to the first / last line
-template <typename R, typename V>
-__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, V v, R* ss, int* bad) {
+template <typename R, typename V, typename Acc>
+__device__ __forceinline__ void scalar_put(const SweepArgs<R>& S, int cc, int i, int j, int k, V v, Acc& ss, int* bad) {
   put(S, 1 + cc, face_idx(S.g, cc, i, j, k), v, ss, bad);
   scalar_walls(S, cc, i, j, k);
 }
 
-template <typename R, int D, int KIND>
-__device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, R* ss, int* bad) {
+// coefficients (a_m, b_m, c_m) of row m of a transverse scalar line, the
+// no-slip fold at the walls of a walled line included
+template <typename R>
+__device__ __forceinline__ void scalar_row(const SweepArgs<R>& S, int cc, int d, int n, int cyc, int a, int b, int m,
+                                           R& am, R& bm, R& cm) {
+  int i, j, k;
+  line_pos(d, a, b, m, i, j, k);
+  R w[3];
+  row_s(S.g, S.P, S.c, S.ub, cc, d, i, j, k, w);
+  am = S.h * w[0]; bm = R(1) + S.h * w[1]; cm = S.h * w[2];
+  if (!cyc) {
+    if (m == 0) { bm -= am; am = R(0); }
+    if (m == n - 1) { bm -= cm; cm = R(0); }
+  }
+}
+
+// One transverse scalar line (component trans_comp(D, KIND)) along D: Thomas,
+// Sherman-Morrison-corrected on a cyclic line; TR: the transposed system.
+template <typename R, int D, int KIND, bool TR = false>
+__device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, SqSum<R>& ss, int* bad) {
   const Geo<R>& g = S.g;
   constexpr int d = D, kind = KIND;
   int cc = trans_comp(d, kind);
@@ -773,14 +910,21 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, R* ss
   for (int m = 0; m < n; m++) {
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    R w[3];
-    row_s(g, S.P, S.c, S.ub, cc, d, i, j, k, w);
-    R am = S.h * w[0], bm = R(1) + S.h * w[1], cm = S.h * w[2];
-    R zr = R(0);
-    if (!cyc) {
-      if (m == 0) { bm -= am; am = R(0); }
-      if (m == n - 1) { bm -= cm; cm = R(0); }
+    R am, bm, cm;
+    if constexpr (TR) {
+      // row m of the transpose: c_{m-1}, b_m, a_{m+1} (wrapping when cyclic)
+      R x0, x1, x2;
+      scalar_row(S, cc, d, n, cyc, a, b, m, x0, bm, x2);
+      am = cm = R(0);
+      int mp = m - 1, mn = m + 1;
+      if (cyc) { mp = mp < 0 ? n - 1 : mp; mn = mn == n ? 0 : mn; }
+      if (mp >= 0) scalar_row(S, cc, d, n, cyc, a, b, mp, x0, x1, am);
+      if (mn < n) scalar_row(S, cc, d, n, cyc, a, b, mn, cm, x1, x2);
     } else {
+      scalar_row(S, cc, d, n, cyc, a, b, m, am, bm, cm);
+    }
+    R zr = R(0);
+    if (cyc) {
       // Sherman-Morrison split: gam = -b_0, u = [gam, 0, .., c_{n-1}], v = [1, 0, .., a_0/gam]
       if (m == 0) { a0 = am; gam = -bm; bm -= gam; zr = gam; am = R(0); }
       if (m == n - 1) { bm -= a0 * cm / gam; zr = cm; cm = R(0); }
@@ -834,29 +978,29 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, R* ss
   }
 }
 
-template <typename R, int D>
+template <typename R, int D, bool TR = false>
 __global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
   int kind = blockIdx.y;
   int line = blockIdx.x * blockDim.x + threadIdx.x;
-  R ss[5] = {0, 0, 0, 0, 0};
+  SqSum<R> ss;
   int bad = 0;
   if (line < S.nl[kind]) {
     int a = (int)(line / S.nb[kind]) + S.a0[kind];
     int b = (int)(line % S.nb[kind]) + S.b0[kind];
-    if (kind == 0) block_line<R, D>(S, line, a, b, ss, &bad);
-    else if (kind == 1) scalar_line<R, D, 1>(S, line, a, b, ss, &bad);
-    else scalar_line<R, D, 2>(S, line, a, b, ss, &bad);
+    if (kind == 0) block_line<R, D, TR>(S, line, a, b, ss, &bad);
+    else if (kind == 1) scalar_line<R, D, 1, TR>(S, line, a, b, ss, &bad);
+    else scalar_line<R, D, 2, TR>(S, line, a, b, ss, &bad);
   }
   if (bad) atomicOr(S.flag, bad);
   if (S.update) {
     for (int f = 0; f < 5; f++) {
-      R v = ss[f];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0 && v != R(0)) atomicAdd(S.acc + f, f2d(v));
+      double v = ss.warp_total(f);
+      if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(S.acc + f, v);
     }
   }
 }
 
+#include "sph_adjoint.cuh"
 #include "sph_lines.cuh"
 
 // ============================================================== host side
@@ -910,6 +1054,28 @@ struct sph_ctx {
   cudaEvent_t efork, ejoin[3];
   int line_solver;       // SPH_LINES_* for the mixed path
   size_t nscr;           // floats in each bulk scratch buffer
+  // wall data (sph_set_bc): the mean of the t^n and t^{n+1} values of the 18
+  // arrays (FP64, and FP32 in mixed mode) for the tangential ghosts, and the
+  // t^{n+1} normal velocity (c == d entries) copied into U^{n+1,0}
+  int hasbc;
+  size_t woff[18], wtot;   // offsets of the arrays in the buffers (wtot = total)
+  int wset[18];            // which arrays were given
+  double* wmean64;
+  float* wmean32;
+  double* wnext;
+  // adjoint workspace (sph_step_adjoint), allocated on first use
+  int adjK;               // iterates the workspace holds
+  size_t fset;            // doubles of one 5-field set
+  size_t foff[5];         // offsets of the fields in a set
+  double* adjS;           // U^{n+1,k}, k < adjK
+  double* adjW;           // 10 sets: lam_n, lam, mu_r, mu_theta, mu_phi, x_r, x_theta, x_phi, lam_Ubar, spare
+  double* adjC;           // the coefficient planes' accumulators (17 planes)
+  double* tape_d;
+  int* tape_ix;
+  int* tape_li;
+  double* tape_adj;
+  int* adj_info;          // longest tape used
+  int tape_cap, tape_blocks;
 };
 
 #define PROF_CAP 65536
@@ -936,6 +1102,7 @@ extern "C" const char* sph_strerror(int code) {
     case SPH_ERR_NONFINITE: return "non-finite value in the new state (state left at U^n)";
     case SPH_ERR_SINGULAR: return "zero pivot in a line solve (state left at U^n)";
     case SPH_ERR_NOMEM: return "device allocation failed";
+    case SPH_ERR_TAPE: return "adjoint: a thread's tape was too short for its rows";
     default: return "unknown error";
   }
 }
@@ -973,6 +1140,9 @@ static void free_all(sph_ctx* c) {
   bufs_free(c->d64);
   bufs_free(c->d32);
   cudaFree(c->bg); cudaFree(c->acc); cudaFree(c->flag);
+  cudaFree(c->wmean64); cudaFree(c->wmean32); cudaFree(c->wnext);
+  cudaFree(c->adjS); cudaFree(c->adjW); cudaFree(c->adjC);
+  cudaFree(c->tape_d); cudaFree(c->tape_ix); cudaFree(c->tape_li); cudaFree(c->tape_adj); cudaFree(c->adj_info);
   for (int f = 0; f < 5; f++) { cudaFree(c->U[0][f]); cudaFree(c->U[1][f]); cudaFree(c->src[f]); }
   free(c->hmet);
 }
@@ -1258,6 +1428,108 @@ extern "C" int sph_set_iterate(sph_ctx* c, const double* const* fields, int on_d
   return e;
 }
 
+// elements of wall array (component c, wall normal to d)
+static size_t wall_count(const Geo<double>& g, int c, int d) {
+  size_t nr = g.nr, nt = g.nt, np = g.np, npf = g.npf;
+  if (c == 0) return d == 1 ? (nr + 1) * np : d == 2 ? (nr + 1) * nt : nt * np;
+  if (c == 1) return d == 0 ? (nt + 1) * np : d == 2 ? nr * (nt + 1) : nr * np;
+  return d == 0 ? nt * npf : d == 1 ? nr * npf : nr * nt;
+}
+
+extern "C" int sph_set_bc(sph_ctx* c, const double* const* wn, const double* const* wnp1, int on_device) {
+  if (!c) return SPH_ERR_ARG;
+  const Geo<double>& g = c->d64.g;
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return SPH_ERR_CUDA;  // steps in flight read the old data
+  int any = 0;
+  size_t tot = 0;
+  for (int q = 0; q < 18; q++) {
+    int cc = q / 6, d = (q / 2) % 3;
+    int given = (wn && wn[q]) || (wnp1 && wnp1[q]);
+    if (d == 2 && g.per) given = 0;  // no phi walls on a periodic line
+    c->wset[q] = given;
+    c->woff[q] = tot;
+    if (given) { tot += wall_count(g, cc, d); any = 1; }
+  }
+  for (int q = 0; q < 18; q++) { c->d64.g.w[q] = NULL; c->d32.g.w[q] = NULL; }
+  c->d64.g.hasw = c->d32.g.hasw = 0;
+  c->hasbc = 0;
+  cudaFree(c->wmean64); cudaFree(c->wmean32); cudaFree(c->wnext);
+  cudaFree(c->adjS); cudaFree(c->adjW); cudaFree(c->adjC);
+  cudaFree(c->tape_d); cudaFree(c->tape_ix); cudaFree(c->tape_li); cudaFree(c->tape_adj); cudaFree(c->adj_info);
+  c->wmean64 = NULL; c->wmean32 = NULL; c->wnext = NULL;
+  c->wtot = tot;
+  if (!any) return SPH_OK;
+  double* hm = (double*)calloc(tot, sizeof(double));
+  double* hn = (double*)calloc(tot, sizeof(double));
+  float* hf = (float*)calloc(tot, sizeof(float));
+  double* tmp = (double*)malloc(tot * sizeof(double));
+  int e = (hm && hn && hf && tmp) ? SPH_OK : SPH_ERR_NOMEM;
+  for (int q = 0; q < 18 && !e; q++) {
+    if (!c->wset[q]) continue;
+    size_t n = wall_count(g, q / 6, (q / 2) % 3), o = c->woff[q];
+    for (int lev = 0; lev < 2 && !e; lev++) {
+      const double* src = lev == 0 ? (wn ? wn[q] : NULL) : (wnp1 ? wnp1[q] : NULL);
+      if (!src) continue;
+      if (on_device) {
+        if (cudaMemcpy(tmp, src, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) { e = SPH_ERR_CUDA; break; }
+        src = tmp;
+      }
+      for (size_t t = 0; t < n; t++) {
+        hm[o + t] += 0.5 * src[t];
+        if (lev == 1) hn[o + t] = src[t];
+      }
+    }
+    for (size_t t = 0; t < n; t++) hf[o + t] = (float)hm[o + t];
+  }
+  if (!e && (cudaMalloc((void**)&c->wmean64, tot * sizeof(double)) != cudaSuccess ||
+             cudaMalloc((void**)&c->wnext, tot * sizeof(double)) != cudaSuccess ||
+             (c->prec == SPH_PREC_MIXED && cudaMalloc((void**)&c->wmean32, tot * sizeof(float)) != cudaSuccess)))
+    e = SPH_ERR_NOMEM;
+  if (!e && (cudaMemcpy(c->wmean64, hm, tot * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(c->wnext, hn, tot * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+             (c->wmean32 && cudaMemcpy(c->wmean32, hf, tot * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)))
+    e = SPH_ERR_CUDA;
+  free(hm); free(hn); free(hf); free(tmp);
+  if (e) { cudaGetLastError(); return e; }
+  for (int q = 0; q < 18; q++) {
+    if (!c->wset[q]) continue;
+    c->d64.g.w[q] = c->wmean64 + c->woff[q];
+    if (c->wmean32) c->d32.g.w[q] = c->wmean32 + c->woff[q];
+  }
+  c->d64.g.hasw = 1;
+  c->d32.g.hasw = c->wmean32 ? 1 : 0;
+  c->hasbc = 1;
+  return SPH_OK;
+}
+
+// U^{n+1,0} = U^n with the t^{n+1} normal velocity on the wall faces (wall
+// data set by sph_set_bc; the c == d arrays), in the iterate buffer
+static int bc_first_iterate(sph_ctx* c) {
+  const Geo<double>& g = c->d64.g;
+  double** un = c->U[c->cur];
+  double** uk = c->U[1 - c->cur];
+  for (int f = 0; f < 5; f++)
+    if (cudaMemcpyAsync(uk[f], un[f], c->nf[f] * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      return SPH_ERR_CUDA;
+  size_t nr = g.nr, nt = g.nt, np = g.np, npf = g.npf, D = sizeof(double);
+  for (int s = 0; s < 2; s++) {
+    int q;
+    if (c->wset[q = (0 * 3 + 0) * 2 + s] &&   // u_r on the r-faces 0 / nr: one contiguous plane
+        cudaMemcpyAsync(uk[1] + (s ? nr : 0) * nt * np, c->wnext + c->woff[q], nt * np * D, cudaMemcpyDeviceToDevice,
+                        c->st) != cudaSuccess)
+      return SPH_ERR_CUDA;
+    if (c->wset[q = (1 * 3 + 1) * 2 + s] &&   // u_theta on the theta-faces 0 / nt: np values per r index
+        cudaMemcpy2DAsync(uk[2] + (s ? nt : 0) * np, (nt + 1) * np * D, c->wnext + c->woff[q], np * D, np * D, nr,
+                          cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      return SPH_ERR_CUDA;
+    if (!g.per && c->wset[q = (2 * 3 + 2) * 2 + s] &&   // u_phi on the phi-faces 0 / np: one value per line
+        cudaMemcpy2DAsync(uk[3] + (s ? np : 0), npf * D, c->wnext + c->woff[q], D, D, nr * nt,
+                          cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      return SPH_ERR_CUDA;
+  }
+  return SPH_OK;
+}
+
 template <typename R> static CF<R> cf_of(R* const* p) { CF<R> r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
 template <typename R> static MF<R> mf_of(R* const* p) { MF<R> r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
 
@@ -1318,9 +1590,9 @@ static int grid_stride_blocks(long n) {
 
 // Ubar into the bulk buffer (FP64 mode at k = 0: U^n itself); coefficients
 template <typename R>
-static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out) {
+static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out, double* const* ukp = nullptr) {
   double** un = c->U[c->cur];
-  double** uk = have_iter ? c->U[1 - c->cur] : un;
+  double* const* uk = have_iter ? (ukp ? ukp : c->U[1 - c->cur]) : un;
   CF<R> ub;
   if (sizeof(R) == sizeof(double) && !have_iter) {
     for (int f = 0; f < 5; f++) ub.f[f] = (const R*)un[f];
@@ -1688,12 +1960,17 @@ static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> s
   double** un = c->U[c->cur];
   double** uk = c->U[1 - c->cur];
   int e = SPH_OK;
+  // with wall data, U^{n+1,0} differs from U^n on the normal wall faces: it is
+  // formed in the iterate buffer and every iteration reads it from there
+  const int first = c->hasbc ? 1 : 0;
+  if (first) e = bc_first_iterate(c);
   for (int it = 0; it < n_iter && !e; it++) {
     CF<R> ub;
-    e = prepare(c, b, it > 0, &ub);
+    const int iter = it > 0 || first;
+    e = prepare(c, b, iter, &ub);
     if (e) break;
-    CF<double> ukin = cf_of(it == 0 ? un : uk);
-    e = run_rhs(c, b, ub, ukin, it > 0, dt, src, has, mf_of(b.Rb));
+    CF<double> ukin = cf_of(iter ? uk : un);
+    e = run_rhs(c, b, ub, ukin, iter, dt, src, has, mf_of(b.Rb));
     if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, ukin, mf_of(uk));
     if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, ukin, mf_of(uk));
     if (!e && it == n_iter - 1 && cudaMemsetAsync(c->acc, 0, 5 * sizeof(double), c->st) != cudaSuccess) e = SPH_ERR_CUDA;
@@ -1756,6 +2033,233 @@ extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* 
   }
   c->cur = 1 - c->cur;
   c->iterate_set = 0;
+  return SPH_OK;
+}
+
+// ------------------------------------------------------------ adjoint
+
+#define ADJ_TAPE_CAP 1536      // nodes per thread's tape
+#define ADJ_TAPE_BLOCKS 304    // blocks of 128 threads of the gradient kernels (two per SM)
+#define ADJ_FLAG_TAPE 8
+
+static int adj_alloc(sph_ctx* c, int K) {
+  if (c->adjS && c->adjK >= K) return SPH_OK;
+  cudaFree(c->adjS);
+  c->adjS = NULL;
+  c->adjK = 0;
+  size_t fs = 0;
+  for (int f = 0; f < 5; f++) { c->foff[f] = fs; fs += c->nf[f]; }
+  c->fset = fs;
+  if (cudaMalloc((void**)&c->adjS, (size_t)K * fs * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return SPH_ERR_NOMEM; }
+  c->adjK = K;
+  if (c->adjW) return SPH_OK;
+  size_t slots = (size_t)ADJ_TAPE_BLOCKS * 128, cap = ADJ_TAPE_CAP;
+  if (cudaMalloc((void**)&c->adjW, 10 * fs * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->adjC, (size_t)NCOEF * c->N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->tape_d, 2 * cap * slots * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->tape_ix, 2 * cap * slots * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->tape_li, cap * slots * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void**)&c->tape_adj, cap * slots * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c->adj_info, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return SPH_ERR_NOMEM;
+  }
+  c->tape_cap = (int)cap;
+  c->tape_blocks = ADJ_TAPE_BLOCKS;
+  return cudaMemset(c->adj_info, 0, sizeof(int)) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+// the 5 fields of set q of a block of sets
+static void adj_set(const sph_ctx* c, double* base, int q, double** out) {
+  for (int f = 0; f < 5; f++) out[f] = base + (size_t)q * c->fset + c->foff[f];
+}
+
+// y += s x over whole 5-field sets
+static int adj_axpy(sph_ctx* c, double s, double* x, double* y) {
+  long n = (long)c->fset;
+  adj::k_axpy<<<grid_stride_blocks(n), 256, 0, c->st>>>(n, s, x, y);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+// the transposed sweep along d: x = P A_d^{-T} P rhs (P: zero on the wall faces)
+static int run_sweep_T(sph_ctx* c, int d, double tau, CF<double> ub, CF<double> rhs, MF<double> x) {
+  Bufs<double>& b = c->d64;
+  SweepArgs<double> S;
+  memset(&S, 0, sizeof S);
+  S.g = b.g; S.P = c->P; S.c = b.c; S.ub = ub; S.d = d; S.h = 0.5 * tau;
+  S.rhs = rhs; S.x = x; S.update = 0;
+  S.scr = b.scr; S.acc = c->acc; S.flag = c->flag;
+  line_layout(c->d64.g, d, S);
+  int mx = S.nl[0];
+  if (S.nl[1] > mx) mx = S.nl[1];
+  if (S.nl[2] > mx) mx = S.nl[2];
+  dim3 grid((unsigned)((mx + 127) / 128), 3);
+  if (d == 0) k_sweep<double, 0, true><<<grid, 128, 0, c->st>>>(S);
+  else if (d == 1) k_sweep<double, 1, true><<<grid, 128, 0, c->st>>>(S);
+  else k_sweep<double, 2, true><<<grid, 128, 0, c->st>>>(S);
+  c->launches++;
+  return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+// the gradient over Ubar of <mu_r, R(Ubar)> - sum_d <mu_d, A_d(Ubar) x_d> into lu
+// (5 fields, added to), by the tape kernels of sph_adjoint.cuh
+static int adj_gradient(sph_ctx* c, double tau, CF<double> ub, double** mu, double** xs, double** lu) {
+  Bufs<double>& b = c->d64;
+  adj::AdjArgs A;
+  memset(&A, 0, sizeof A);
+  A.g = b.g; A.P = c->P; A.c = b.c; A.ub = ub; A.tau = tau;
+  for (int d = 0; d < 3; d++) {
+    double* m5[5];
+    double* x5[5];
+    adj_set(c, mu[d], 0, m5);
+    adj_set(c, xs[d], 0, x5);
+    A.mu[d] = cf_of(m5);
+    A.x[d] = cf_of(x5);
+  }
+  for (int f = 0; f < 5; f++) A.lam[f] = lu[f];
+  for (int q = 0; q < NCOEF; q++) A.lam[5 + q] = c->adjC + (size_t)q * c->N;
+  A.td = c->tape_d; A.tix = c->tape_ix; A.tli = c->tape_li; A.tadj = c->tape_adj; A.cap = c->tape_cap;
+  A.flag = c->flag; A.maxn = c->adj_info;
+  if (cudaMemsetAsync(c->adjC, 0, (size_t)NCOEF * c->N * sizeof(double), c->st) != cudaSuccess) return SPH_ERR_CUDA;
+  const int nb = c->tape_blocks;
+  for (int kind = 0; kind < 4; kind++) adj::k_adj_rhs<<<nb, 128, 0, c->st>>>(A, kind);
+  for (int d = 0; d < 3; d++) {
+    SweepArgs<double> S;
+    memset(&S, 0, sizeof S);
+    line_layout(c->d64.g, d, S);
+    if (d == 0) {
+      adj::k_adj_blk<0><<<nb, 128, 0, c->st>>>(A, S.nl[0], S.nb[0], S.a0[0], S.b0[0]);
+      adj::k_adj_sca<0, 1><<<nb, 128, 0, c->st>>>(A, S);
+      adj::k_adj_sca<0, 2><<<nb, 128, 0, c->st>>>(A, S);
+    } else if (d == 1) {
+      adj::k_adj_blk<1><<<nb, 128, 0, c->st>>>(A, S.nl[0], S.nb[0], S.a0[0], S.b0[0]);
+      adj::k_adj_sca<1, 1><<<nb, 128, 0, c->st>>>(A, S);
+      adj::k_adj_sca<1, 2><<<nb, 128, 0, c->st>>>(A, S);
+    } else {
+      adj::k_adj_blk<2><<<nb, 128, 0, c->st>>>(A, S.nl[0], S.nb[0], S.a0[0], S.b0[0]);
+      adj::k_adj_sca<2, 1><<<nb, 128, 0, c->st>>>(A, S);
+      adj::k_adj_sca<2, 2><<<nb, 128, 0, c->st>>>(A, S);
+    }
+  }
+  adj::k_adj_coef<<<nb, 128, 0, c->st>>>(A);
+  c->launches += 14;
+  return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+extern "C" int sph_step_adjoint(sph_ctx* c, double dt, int n_iter, const double* const* source,
+                                const double* const* lam_out, double* const* lam_in) {
+  if (!c || !(dt > 0) || n_iter < 1 || !lam_out || !lam_in) return SPH_ERR_ARG;
+  if (c->prec != SPH_PREC_FP64) return SPH_ERR_ARG;
+  for (int f = 0; f < 5; f++)
+    if (!lam_out[f] || !lam_in[f]) return SPH_ERR_ARG;
+  int e = adj_alloc(c, n_iter);
+  if (e) return e;
+  if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->st) != cudaSuccess) return SPH_ERR_CUDA;
+  CF<double> src;
+  int has = stage_source(c, source, 1, &src);
+  Bufs<double>& b = c->d64;
+  double** un = c->U[c->cur];
+  const size_t FB = c->fset * sizeof(double);
+  double *LN[5], *LB[5], *MU[3][5], *XS[3][5], *LU[5];
+  adj_set(c, c->adjW, 0, LN);
+  adj_set(c, c->adjW, 1, LB);
+  for (int d = 0; d < 3; d++) { adj_set(c, c->adjW, 2 + d, MU[d]); adj_set(c, c->adjW, 5 + d, XS[d]); }
+  adj_set(c, c->adjW, 8, LU);
+  double* mu_base[3] = {MU[0][0], MU[1][0], MU[2][0]};
+  double* x_base[3] = {XS[0][0], XS[1][0], XS[2][0]};
+  // forward: the iterates U^{n+1,k}, k < K (U^{n+1,0} = U^n, with the t^{n+1}
+  // normal wall velocity when wall data are set)
+  double* S0[5];
+  adj_set(c, c->adjS, 0, S0);
+  for (int f = 0; f < 5 && !e; f++)
+    if (cudaMemcpyAsync(S0[f], un[f], c->nf[f] * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      e = SPH_ERR_CUDA;
+  if (!e && c->hasbc) {
+    // the wall faces of the iterate buffer, written by bc_first_iterate, into S0
+    e = bc_first_iterate(c);
+    for (int f = 0; f < 5 && !e; f++)
+      if (cudaMemcpyAsync(S0[f], c->U[1 - c->cur][f], c->nf[f] * sizeof(double), cudaMemcpyDeviceToDevice, c->st) !=
+          cudaSuccess)
+        e = SPH_ERR_CUDA;
+  }
+  const int first = c->hasbc ? 1 : 0;
+  for (int k = 0; k + 1 < n_iter && !e; k++) {
+    double *Sk[5], *Sn[5];
+    adj_set(c, c->adjS, k, Sk);
+    adj_set(c, c->adjS, k + 1, Sn);
+    const int iter = k > 0 || first;
+    CF<double> ub;
+    e = prepare(c, b, iter, &ub, Sk);
+    if (!e) e = run_rhs(c, b, ub, cf_of(iter ? Sk : un), iter, dt, src, has, mf_of(b.Rb));
+    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, cf_of(Sk), mf_of(Sn));
+    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, cf_of(Sk), mf_of(Sn));
+    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(Sn), 1, cf_of(Sk), mf_of(Sn));
+  }
+  // reverse
+  if (!e && cudaMemsetAsync(LN[0], 0, FB, c->st) != cudaSuccess) e = SPH_ERR_CUDA;
+  for (int f = 0; f < 5 && !e; f++)
+    if (cudaMemcpyAsync(LB[f], lam_out[f], c->nf[f] * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      e = SPH_ERR_CUDA;
+  for (int k = n_iter - 1; k >= 0 && !e; k--) {
+    double* Sk[5];
+    adj_set(c, c->adjS, k, Sk);
+    const int iter = k > 0 || first;
+    CF<double> ub;
+    // the iteration's Ubar, coefficients and sweep solutions
+    e = prepare(c, b, iter, &ub, Sk);
+    if (!e) e = run_rhs(c, b, ub, cf_of(iter ? Sk : un), iter, dt, src, has, mf_of(b.Rb));
+    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(XS[0]), 0, cf_of(Sk), mf_of(Sk));
+    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(XS[0]), mf_of(XS[1]), 0, cf_of(Sk), mf_of(Sk));
+    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(XS[1]), mf_of(XS[2]), 0, cf_of(Sk), mf_of(Sk));
+    // transposed solves, phi first
+    if (!e) e = run_sweep_T(c, 2, dt, ub, cf_of(LB), mf_of(MU[2]));
+    if (!e) e = run_sweep_T(c, 1, dt, ub, cf_of(MU[2]), mf_of(MU[1]));
+    if (!e) e = run_sweep_T(c, 0, dt, ub, cf_of(MU[1]), mf_of(MU[0]));
+    // R = -(b - a) - tau N: dJ/da += mu_r, dJ/db -= mu_r
+    if (!e) e = adj_axpy(c, 1.0, MU[0][0], LN[0]);
+    if (!e) e = adj_axpy(c, -1.0, MU[0][0], LB[0]);
+    // the Ubar dependence, half to each of a and b
+    if (!e && cudaMemsetAsync(LU[0], 0, FB, c->st) != cudaSuccess) e = SPH_ERR_CUDA;
+    if (!e) e = adj_gradient(c, dt, ub, mu_base, x_base, LU);
+    if (!e) e = adj_axpy(c, 0.5, LU[0], LN[0]);
+    if (!e) e = adj_axpy(c, 0.5, LU[0], LB[0]);
+  }
+  if (!e && c->hasbc) {
+    // U^{n+1,0}'s normal wall faces were data, not U^n
+    const Geo<double>& g = c->d64.g;
+    size_t nr = g.nr, nt = g.nt, np = g.np, npf = g.npf, D = sizeof(double);
+    for (int s = 0; s < 2 && !e; s++) {
+      if (c->wset[(0 * 3 + 0) * 2 + s] &&
+          cudaMemsetAsync(LB[1] + (s ? nr : 0) * nt * np, 0, nt * np * D, c->st) != cudaSuccess) e = SPH_ERR_CUDA;
+      if (!e && c->wset[(1 * 3 + 1) * 2 + s] &&
+          cudaMemset2DAsync(LB[2] + (s ? nt : 0) * np, (nt + 1) * np * D, 0, np * D, nr, c->st) != cudaSuccess)
+        e = SPH_ERR_CUDA;
+      if (!e && !g.per && c->wset[(2 * 3 + 2) * 2 + s] &&
+          cudaMemset2DAsync(LB[3] + (s ? np : 0), npf * D, 0, D, nr * nt, c->st) != cudaSuccess)
+        e = SPH_ERR_CUDA;
+    }
+  }
+  if (!e) e = adj_axpy(c, 1.0, LB[0], LN[0]);
+  for (int f = 0; f < 5 && !e; f++)
+    if (cudaMemcpyAsync(lam_in[f], LN[f], c->nf[f] * sizeof(double), cudaMemcpyDeviceToDevice, c->st) != cudaSuccess)
+      e = SPH_ERR_CUDA;
+  if (e) return e;
+  int flag = 0;
+  if ((e = read_flag(c, &flag))) return e;
+  if (flag & ADJ_FLAG_TAPE) return SPH_ERR_TAPE;
+  if (flag & FLAG_SINGULAR) return SPH_ERR_SINGULAR;
+  return SPH_OK;
+}
+
+extern "C" int sph_adjoint_tape_use(sph_ctx* c, int* longest, int* capacity) {
+  if (!c) return SPH_ERR_ARG;
+  int n = 0;
+  if (c->adj_info && (cudaStreamSynchronize(c->st) != cudaSuccess ||
+                      cudaMemcpy(&n, c->adj_info, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess))
+    return SPH_ERR_CUDA;
+  if (longest) *longest = n;
+  if (capacity) *capacity = c->adj_info ? c->tape_cap : ADJ_TAPE_CAP;
   return SPH_OK;
 }
 

@@ -22,27 +22,70 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace sph {
+
+// Value-type traits of the row templates.  R is the kernels' bulk type (float
+// or double) or the adjoint's tape value: T is the type of the metric tables and
+// of the grid spacings, CP what a row reads a field or a coefficient plane
+// through, MP what the coefficient stage writes a plane through.  For float and
+// double these are the plain types and pointers; the adjoint specialises them
+// (tables stay double, reads record tape leaves).
+template <typename R>
+struct Val {
+  using T = R;
+  using CP = const R*;
+  using MP = R*;
+};
+template <typename R> using TabT = typename Val<R>::T;
+// whether R is the FP32 bulk type (the mixed mode's pair arithmetic) or an
+// FP64 value (double, or the adjoint's tape value on doubles)
+template <typename R> constexpr bool is_f32 = std::is_same<R, float>::value;
 
 template <typename R>
 struct Geo {
+  using T = TabT<R>;
   int nr, nt, np, npf, per;
-  R dr, dth, dph, idr, idth, idph;
+  T dr, dth, dph, idr, idth, idph;
   // metric tables: centres rc[nr], faces rf[nr+1]; theta centres/faces
-  const R *rc, *rf, *irc, *irf;
-  const R *sc, *sf, *isc, *isf, *cc, *cf, *cotc, *cotf;
+  const T *rc, *rf, *irc, *irf;
+  const T *sc, *sf, *isc, *isf, *cc, *cf, *cotc, *cotf;
   // radial background (index i+1 for i in [-1, nr]) and derived tables
   const double *bgp, *bgT;   // p_ref, T_ref (FP64, full values)
-  const R* dbgp;             // [nr]   p_ref[i+1] - p_ref[i-1]
-  const R* dbgT;             // [nr]   T_ref[i+1] - T_ref[i-1]
-  const R* lapT;             // [nr]   (rf_{i+1}^2 (T_{i+1}-T_i) - rf_i^2 (T_i-T_{i-1})) / (rc^2 dr^2)
-  const R* rhoref;           // [nr]   (p_ref + pi_inf) / (Rg T_ref)
-  const R* ehyd;             // [nr+1] (p_ref[i]-p_ref[i-1]) / (dr rho_ref,f) + g on interior r-faces
-  const R* pcen;             // [nr]   p_ref + pi_inf at the centres
-  const R* Tcen;             // [nr]   T_ref at the centres
+  const T* dbgp;             // [nr]   p_ref[i+1] - p_ref[i-1]
+  const T* dbgT;             // [nr]   T_ref[i+1] - T_ref[i-1]
+  const T* lapT;             // [nr]   (rf_{i+1}^2 (T_{i+1}-T_i) - rf_i^2 (T_i-T_{i-1})) / (rc^2 dr^2)
+  const T* rhoref;           // [nr]   (p_ref + pi_inf) / (Rg T_ref)
+  const T* ehyd;             // [nr+1] (p_ref[i]-p_ref[i-1]) / (dr rho_ref,f) + g on interior r-faces
+  const T* pcen;             // [nr]   p_ref + pi_inf at the centres
+  const T* Tcen;             // [nr]   T_ref at the centres
   // rf^2 and sin(theta_f) as hi + lo pairs (lo = 0 in FP64), for div(Ubar)
-  const R *rf2h, *rf2l, *sfh, *sfl;
+  const T *rf2h, *rf2l, *sfh, *sfl;
+  // Dirichlet wall data of Ubar for the tangential ghosts (ghost = 2 w - the
+  // interior value): w[(c*3 + d)*2 + s] is velocity component c on the wall
+  // normal to direction d at side s, the mean of its t^n and t^{n+1} values
+  // (NULL entries are 0; hasw = 0 means homogeneous walls everywhere).
+  // Layouts: c = r: d = theta (nr+1)*np, d = phi (nr+1)*nt; c = theta:
+  // d = r (nt+1)*np, d = phi nr*(nt+1); c = phi: d = r nt*npf, d = theta nr*npf.
+  const T* w[18];
+  int hasw;
 };
+
+// twice the wall value of component c on the wall normal to d at side s
+// (0 for homogeneous walls)
+// (c and d are constants at every call, so both candidate arrays are fixed
+// parameter slots and the side only selects between them: no dynamic index
+// into the kernel's parameters)
+template <typename G>
+__device__ __forceinline__ auto wall2(const G& g, int c, int d, int s, int idx) -> decltype(+*g.w[0]) {
+  using V = decltype(+*g.w[0]);
+  if (!g.hasw) return V(0);
+  const auto* lo = g.w[(c * 3 + d) * 2];
+  const auto* hi = g.w[(c * 3 + d) * 2 + 1];
+  const auto* a = s ? hi : lo;
+  return a ? V(2) * a[idx] : V(0);
+}
 
 struct Par {
   double gamma, cv, Pr, mu, pinf, g, omega;
@@ -134,16 +177,17 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 
 template <typename R>
 struct Coef {  // per cell centre, frozen at Ubar
-  R *Pb, *Tb, *rho, *drho, *beta, *uc0, *uc1, *uc2;
-  R *grr, *gtt, *gpp, *srt, *srp, *stp;  // G_rr, G_tt, G_pp, G_rt+G_tr, G_rp+G_pr, G_tp+G_pt
+  using MP = typename Val<R>::MP;
+  MP Pb, Tb, rho, drho, beta, uc0, uc1, uc2;
+  MP grr, gtt, gpp, srt, srp, stp;  // G_rr, G_tt, G_pp, G_rt+G_tr, G_rp+G_pr, G_tp+G_pt
   // the three parts of div(Ubar) at the centre, (1/r^2) d_r (r^2 u_r),
   // (1/(r sin)) d_t (sin u_t), (1/(r sin)) d_p u_p, for the grad-div viscous
   // terms of the momentum rows (each row reads them at its two centres)
-  R *dvr, *dvt, *dvp;
+  MP dvr, dvt, dvp;
 };
 constexpr int NCOEF = 17;
 
-template <typename R> struct CF { const R* f[5]; };
+template <typename R> struct CF { typename Val<R>::CP f[5]; };
 template <typename R> struct MF { R* f[5]; };
 
 // 32-bit flat indices: the host refuses grids whose arrays (and line-solve
@@ -166,53 +210,56 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // do not diverge); k (phi) is always checked.
 //
 // Centre perturbation with zero Neumann ghosts (the background has its own).
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R cpert(const G& g, const R* f, int i, int j, int k) {
+template <typename P> using ValOf = typename std::decay<decltype(std::declval<P>()[0])>::type;
+
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> cpert(const G& g, const P& f, int i, int j, int k) {
   int ii = CIJ ? clampi(i, 0, g.nr - 1) : i, jj = CIJ ? clampi(j, 0, g.nt - 1) : j;
   int kk = g.per ? wrapk(g, k) : clampi(k, 0, g.np - 1);
   return f[IC(g, ii, jj, kk)];
 }
-// Velocities with no-slip ghosts (ghost = -interior) on tangential walls.
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R vr(const G& g, const R* u, int i, int j, int k) {
-  if (CIJ && j < 0) return -u[IRf(g, i, 0, k)];
-  if (CIJ && j >= g.nt) return -u[IRf(g, i, g.nt - 1, k)];
+// Velocities with Dirichlet ghosts on tangential walls: ghost = 2 w - interior
+// (w = 0, no-slip, unless wall data were set).
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> vr(const G& g, const P& u, int i, int j, int k) {
+  if (CIJ && j < 0) return wall2(g, 0, 1, 0, i * g.np + k) - u[IRf(g, i, 0, k)];
+  if (CIJ && j >= g.nt) return wall2(g, 0, 1, 1, i * g.np + k) - u[IRf(g, i, g.nt - 1, k)];
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
-    else return -u[IRf(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else return wall2(g, 0, 2, k >= g.np, i * g.nt + j) - u[IRf(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return u[IRf(g, i, j, k)];
 }
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R vt(const G& g, const R* u, int i, int j, int k) {
-  if (CIJ && i < 0) return -u[ITf(g, 0, j, k)];
-  if (CIJ && i >= g.nr) return -u[ITf(g, g.nr - 1, j, k)];
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> vt(const G& g, const P& u, int i, int j, int k) {
+  if (CIJ && i < 0) return wall2(g, 1, 0, 0, j * g.np + k) - u[ITf(g, 0, j, k)];
+  if (CIJ && i >= g.nr) return wall2(g, 1, 0, 1, j * g.np + k) - u[ITf(g, g.nr - 1, j, k)];
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
-    else return -u[ITf(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else return wall2(g, 1, 2, k >= g.np, i * (g.nt + 1) + j) - u[ITf(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return u[ITf(g, i, j, k)];
 }
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R vp(const G& g, const R* u, int i, int j, int k) {
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> vp(const G& g, const P& u, int i, int j, int k) {
   if (g.per) k = wrapk(g, k);
-  if (CIJ && i < 0) return -u[IPf(g, 0, j, k)];
-  if (CIJ && i >= g.nr) return -u[IPf(g, g.nr - 1, j, k)];
-  if (CIJ && j < 0) return -u[IPf(g, i, 0, k)];
-  if (CIJ && j >= g.nt) return -u[IPf(g, i, g.nt - 1, k)];
+  if (CIJ && i < 0) return wall2(g, 2, 0, 0, j * g.npf + k) - u[IPf(g, 0, j, k)];
+  if (CIJ && i >= g.nr) return wall2(g, 2, 0, 1, j * g.npf + k) - u[IPf(g, g.nr - 1, j, k)];
+  if (CIJ && j < 0) return wall2(g, 2, 1, 0, i * g.npf + k) - u[IPf(g, i, 0, k)];
+  if (CIJ && j >= g.nt) return wall2(g, 2, 1, 1, i * g.npf + k) - u[IPf(g, i, g.nt - 1, k)];
   return u[IPf(g, i, j, k)];
 }
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R hr(const G& g, const R* u, int i, int j, int k) {
-  return R(0.5) * (vr<CIJ>(g, u, i, j, k) + vr<CIJ>(g, u, i + 1, j, k));
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> hr(const G& g, const P& u, int i, int j, int k) {
+  return ValOf<P>(0.5) * (vr<CIJ>(g, u, i, j, k) + vr<CIJ>(g, u, i + 1, j, k));
 }
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R ht(const G& g, const R* u, int i, int j, int k) {
-  return R(0.5) * (vt<CIJ>(g, u, i, j, k) + vt<CIJ>(g, u, i, j + 1, k));
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> ht(const G& g, const P& u, int i, int j, int k) {
+  return ValOf<P>(0.5) * (vt<CIJ>(g, u, i, j, k) + vt<CIJ>(g, u, i, j + 1, k));
 }
-template <bool CIJ = true, typename G, typename R>
-__device__ __forceinline__ R hp(const G& g, const R* u, int i, int j, int k) {
-  return R(0.5) * (vp<CIJ>(g, u, i, j, k) + vp<CIJ>(g, u, i, j, k + 1));
+template <bool CIJ = true, typename G, typename P>
+__device__ __forceinline__ ValOf<P> hp(const G& g, const P& u, int i, int j, int k) {
+  return ValOf<P>(0.5) * (vp<CIJ>(g, u, i, j, k) + vp<CIJ>(g, u, i, j, k + 1));
 }
 template <typename R>
 __device__ __forceinline__ R rho_at(const Geo<R>& g, const Coef<R>& c, int i, int j, int k) {
@@ -222,31 +269,37 @@ __device__ __forceinline__ R rho_at(const Geo<R>& g, const Coef<R>& c, int i, in
 
 // A velocity component averaged to centre (i, j, k): in interior blocks
 // (CIJ = false) read from the coefficient plane k_coef wrote (uc0/uc1/uc2, the
-// same FP32 operations, so the same value), with the no-slip ghost -- minus the
-// mirrored centre -- beyond a phi wall and the periodic wrap (only used for
-// components tangential to phi); elsewhere the face average with all checks.
-template <typename R>
-__device__ __forceinline__ R ucen(const Geo<R>& g, const R* plane, int i, int j, int k) {
+// same FP32 operations, so the same value), with the Dirichlet ghost -- the
+// two faces' 2 w minus the mirrored centre -- beyond a phi wall and the
+// periodic wrap (only used for the components tangential to phi, CC = 0 or 1);
+// elsewhere the face average with all checks.
+template <int CC, typename R>
+__device__ __forceinline__ R ucen(const Geo<R>& g, const typename Val<R>::CP& plane, int i, int j, int k) {
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
-    else return -plane[IC(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else {
+      int s = k >= g.np, kk = s ? g.np - 1 : 0;
+      R w = CC == 0 ? R(0.5) * (wall2(g, 0, 2, s, i * g.nt + j) + wall2(g, 0, 2, s, (i + 1) * g.nt + j))
+                    : R(0.5) * (wall2(g, 1, 2, s, i * (g.nt + 1) + j) + wall2(g, 1, 2, s, i * (g.nt + 1) + j + 1));
+      return w - plane[IC(g, i, j, kk)];
+    }
   }
   return plane[IC(g, i, j, k)];
 }
-template <bool CIJ, typename R>
-__device__ __forceinline__ R hrc(const Geo<R>& g, const Coef<R>& c, const R* u, int i, int j, int k) {
+template <bool CIJ, typename R, typename P>
+__device__ __forceinline__ R hrc(const Geo<R>& g, const Coef<R>& c, const P& u, int i, int j, int k) {
   if constexpr (CIJ) return hr<true>(g, u, i, j, k);
-  else return ucen(g, (const R*)c.uc0, i, j, k);
+  else return ucen<0>(g, c.uc0, i, j, k);
 }
-template <bool CIJ, typename R>
-__device__ __forceinline__ R htc(const Geo<R>& g, const Coef<R>& c, const R* u, int i, int j, int k) {
+template <bool CIJ, typename R, typename P>
+__device__ __forceinline__ R htc(const Geo<R>& g, const Coef<R>& c, const P& u, int i, int j, int k) {
   if constexpr (CIJ) return ht<true>(g, u, i, j, k);
-  else return ucen(g, (const R*)c.uc1, i, j, k);
+  else return ucen<1>(g, c.uc1, i, j, k);
 }
-template <bool CIJ, typename R>
-__device__ __forceinline__ R hpc(const Geo<R>& g, const Coef<R>& c, const R* u, int i, int j, int k) {
+template <bool CIJ, typename R, typename P>
+__device__ __forceinline__ R hpc(const Geo<R>& g, const Coef<R>& c, const P& u, int i, int j, int k) {
   if constexpr (CIJ) return hp<true>(g, u, i, j, k);
-  else return ucen(g, (const R*)c.uc2, i, j, k);
+  else return ucen<2>(g, c.uc2, i, j, k);
 }
 
 // whether the +-2 neighbourhood of (i, j) in r and theta is inside the grid
@@ -383,7 +436,8 @@ template <typename R>
 struct FPt { R rho0, rho1, ub; };
 
 template <typename R>
-__device__ __forceinline__ FPt<R> load_f(const Geo<R>& g, const Coef<R>& c, const R* ubd, int d, int i, int j, int k) {
+__device__ __forceinline__ FPt<R> load_f(const Geo<R>& g, const Coef<R>& c, const typename Val<R>::CP& ubd, int d, int i,
+                                         int j, int k) {
   FPt<R> q;
   if (d == 0) {
     q.rho0 = rho_at(g, c, i - 1, j, k); q.rho1 = rho_at(g, c, i, j, k); q.ub = ubd[IRf(g, i, j, k)];
@@ -432,7 +486,7 @@ __device__ __forceinline__ void row_fw(const Geo<R>& g, const Par& P, const FPt<
 }
 
 template <typename R>
-__device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<R>& c, const R* ubd, int d, int i,
+__device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<R>& c, const typename Val<R>::CP& ubd, int d, int i,
                                       int j, int k, R wp[2], R wu[3]) {
   row_fw(g, P, load_f(g, c, ubd, d, i, j, k), d, i, j, wp, wu);
 }

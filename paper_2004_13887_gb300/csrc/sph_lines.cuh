@@ -301,6 +301,14 @@ __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm
 // reads of the coefficient planes, copied asynchronously like the block
 // lines' inputs; next to them the checked accessors give rho and the mean,
 // which is stored twice (its mean is itself).
+// the checked-accessor path of stage_scalar (cells next to the r and theta
+// walls), out of line: inlined into the unrolled staging loop its wall-data
+// branches would crowd the 48-register budget of the scalar kernels
+template <int D, int KIND>
+__device__ __noinline__ SPt<float> stage_scalar_edge(const SweepArgs<float>& S, int i, int j, int k) {
+  return load_s<true>(S.g, S.c, S.ub, trans_comp(D, KIND), D, i, j, k);
+}
+
 template <int D, int KIND, int FS>
 __device__ __forceinline__ void stage_scalar(const SweepArgs<float>& S, float* sm, int si, int a, int b, int c) {
   const Geo<float>& g = S.g;
@@ -315,7 +323,7 @@ __device__ __forceinline__ void stage_scalar(const SweepArgs<float>& S, float* s
     cpa4(sm + 0 * FS + si, S.c.rho + c0); cpa4(sm + 1 * FS + si, S.c.rho + c1);
     cpa4(sm + 2 * FS + si, ua + c0); cpa4(sm + 3 * FS + si, ua + c1);
   } else {
-    SPt<float> q = load_s<true>(g, S.c, S.ub, cc, D, i, j, k);
+    SPt<float> q = stage_scalar_edge<D, KIND>(S, i, j, k);
     sm[0 * FS + si] = q.rho0; sm[1 * FS + si] = q.rho1; sm[2 * FS + si] = q.ua; sm[3 * FS + si] = q.ua;
   }
   cpa4(sm + 4 * FS + si, S.rhs.f[1 + cc] + face_idx(g, cc, i, j, k));
@@ -334,14 +342,14 @@ __device__ __forceinline__ Group group_of(const SweepArgs<float>& S, int kind, i
   return G;
 }
 
-__device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, float* ss, int bad) {
+template <typename Acc>
+__device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, const Acc& ss, int bad) {
   if (bad) atomicOr(S.flag, bad);
   if (S.update) {
 #pragma unroll
     for (int f = 0; f < 5; f++) {
-      float v = ss[f];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-      if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(S.acc + f, f2d(v));
+      double v = ss.warp_total(f);
+      if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(S.acc + f, v);
     }
   }
 }
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
   const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31;  // warp, lane of the warp
   const int w = threadIdx.x / L, lane = threadIdx.x % L;    // block line, lane of the line
   const float h = S.h;
-  float ss[5] = {0, 0, 0, 0, 0};
+  SqSum<float> ss;
   int bad = 0;
   float* slot = S.scr + ((size_t)blockIdx.x * SH::NWW + wid) * (32 * slot_floats(P));
   float* xb = sm + 3 * FS;  // lane exchanges of lines longer than a warp (after the elimination)
@@ -643,7 +651,7 @@ __device__ __forceinline__ void lines_sca(const SweepArgs<float>& S, int grp) {
   const int w = threadIdx.x / L, lane = threadIdx.x % L;
   float* xb = sm + FS;  // lane exchanges of lines longer than a warp (after the elimination)
   const float h = S.h;
-  float ss[5] = {0, 0, 0, 0, 0};
+  SqSumLite ss;
   int bad = 0;
   Group G = group_of(S, KIND, grp, NW);
 #pragma unroll

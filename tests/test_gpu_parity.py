@@ -245,6 +245,12 @@ def test_full_size_step():
     for q in range(5):
         err = float(np.max(np.abs(U[q] - Uo[q])))
         assert err <= 1e-12 * scale[q], (q, err, scale[q], rel_err(U[q], Uo[q]))
+    # the velocities against their own size as well: the rounding of the
+    # hydrostatic terms, 1e-12 of g dt, would allow ~2e-7 of max|u_r| after two
+    # steps; measured 7e-12 (u_r) and 1e-10 (u_theta, u_phi), bounded at 1e-9
+    rel_u = [rel_err(U[q], Uo[q]) for q in (1, 2, 3)]
+    print("full-size FP64 step vs oracle, velocity max-norm error / max|u|:", rel_u)
+    assert max(rel_u) <= 1e-9, rel_u
 
 
 def test_full_size_step_symmetry():
