@@ -146,7 +146,7 @@ int sph_status(sph_ctx* ctx, double* residual_out);
  * iteration the transposed line solves (phi, theta, r) and the gradient over
  * Ubar of the right-hand side and of the three line operators, by reverse-mode
  * differentiation of the library's own row functions.  Work buffers (about 16
- * fields plus 17 coefficient planes and the per-thread tapes, ~2 GB) are
+ * fields plus 17 coefficient planes and 0.7 GB of per-thread tapes) are
  * allocated on the first call and kept with the context.  Synchronises.
  * Errors: SPH_ERR_ARG, SPH_ERR_NOMEM, SPH_ERR_CUDA, SPH_ERR_SINGULAR (a zero pivot
  * in a transposed solve), SPH_ERR_TAPE (a location's rows outgrew the tape). */
@@ -208,8 +208,23 @@ int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double
 #define SPH_LINES_PARTITIONED_WARP 2
 int sph_set_line_solver(sph_ctx* ctx, int which);
 
+/* Tile shape of the stencil kernels (coefficients, right-hand side): blocks of
+ * 128 threads over 128/(tj*ti) phi points x tj theta rows x ti r rows; tj, ti
+ * powers of two with tj*ti <= 8 (SPH_ERR_ARG otherwise).  Default 1 x 1 (one
+ * row of 128 phi points).  The results do not depend on it. */
+int sph_set_tile(sph_ctx* ctx, int tj, int ti);
+
 /* Number of this library's kernel launches since creation (for accounting). */
 long long sph_launch_count(const sph_ctx* ctx);
+
+/* The bounds-checked debug build (compiled with SPH_CHECKED; the stand-in for
+ * a memory checker): every flat index the kernels form from (i, j, k) is
+ * checked against its field's extents; a violation is counted, the access is
+ * redirected to element 0 and the run goes on.  Returns the number of
+ * violations since the last call on the current device and clears it (first:
+ * NULL or 4 ints, the field -- 0 centres, 1 u_r, 2 u_theta, 3 u_phi -- and the
+ * (i, j, k) of the first), synchronising the device; -1 from a regular build. */
+int sph_bounds_report(int* first);
 
 /* Per-kernel timing.  sph_profile(ctx, 1) clears the record and starts timing
  * every kernel stage (one launch, the four of the right-hand side, or the
@@ -253,6 +268,36 @@ const char* sph_strerror(int code);
 #define SPH_NOALLOC_MAX_BLOCKS 131072
 int sph_block_thomas_noalloc(int nlines, int n, const double* A, const double* B, const double* C,
                              const double* d, double* x, void* stream);
+
+/* The partitioned (Schur-complement) block Thomas algorithm for lines whose
+ * blocks are split across P ranks (Section 2.2: the block Thomas algorithm
+ * parallelised by a Schur complement over the subdomains of a line).  Rank p
+ * holds m >= 2 consecutive blocks of each of nlines lines,
+ *   A_i x_{i-1} + B_i x_i + C_i x_{i+1} = d_i,  i = 0..m-1,
+ * where x_{-1} is rank p-1's last block and x_m rank p+1's first (cyclic: rank
+ * 0 and rank P-1 are neighbours; walled: rank 0's A_0 and rank P-1's C_{m-1}
+ * are zero).  Layouts: 3x3 row-major blocks, block (l, i) at (l*m + i)*9 of A,
+ * B, C, V, W and at (l*m + i)*3 of d, Y, x.  Device pointers; nothing is
+ * allocated (the caller passes scratch); work on `stream`; each call
+ * synchronises to report a zero pivot as SPH_ERR_SINGULAR (except back).
+ *  1. sph_schur_local: the segment's own solves T y = d, T V = A_0 e_0,
+ *     T W = C_{m-1} e_{m-1} (T without the outer couplings), so that
+ *     x = y - V x_{-1} - W x_m.  scratch: 30 * nlines * m doubles.
+ *  2. Every rank gathers every rank's interface rows: per line 42 doubles,
+ *     V_0, V_{m-1}, W_0, W_{m-1} (9 each) then y_0, y_{m-1} (3 each), laid out
+ *     iface[(p * nlines + l) * 42 + ...].  sph_schur_reduced solves the 6P x 6P
+ *     system of the ranks' first and last blocks (dense, partial pivoting;
+ *     P <= 8) into z[((l * 2P) + 2p) * 3 + r] (first block of rank p) and
+ *     [.. + 2p + 1 ..] (its last block).
+ *  3. sph_schur_back: x = y - V xl - W xr with xl = rank p-1's last block and
+ *     xr = rank p+1's first block from z (zero past a walled end), 3 values per
+ *     line each.
+ * flag: one device int of scratch. */
+int sph_schur_local(int nlines, int m, const double* A, const double* B, const double* C, const double* d,
+                    double* scratch, double* Y, double* V, double* W, int* flag, void* stream);
+int sph_schur_reduced(int nlines, int P, int cyclic, const double* iface, double* z, int* flag, void* stream);
+int sph_schur_back(int nlines, int m, const double* Y, const double* V, const double* W, const double* xl,
+                   const double* xr, double* x, void* stream);
 
 #ifdef __cplusplus
 }

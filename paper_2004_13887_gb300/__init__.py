@@ -71,12 +71,18 @@ SIGNATURES = {
     "sph_rhs": ([_CTX, C.c_double, _PP, C.c_int, _PP], C.c_int),
     "sph_sweep": ([_CTX, C.c_int, C.c_double, _PP, _PP], C.c_int),
     "sph_set_line_solver": ([_CTX, C.c_int], C.c_int),
+    "sph_set_tile": ([_CTX, C.c_int, C.c_int], C.c_int),
     "sph_launch_count": ([_CTX], C.c_longlong),
+    "sph_bounds_report": ([C.POINTER(C.c_int)], C.c_int),
     "sph_profile": ([_CTX, C.c_int], C.c_int),
     "sph_profile_read": ([_CTX, _DP, C.POINTER(C.c_longlong)], C.c_int),
     "sph_destroy": ([_CTX], None),
     "sph_block_thomas_noalloc": ([C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP, C.c_void_p], C.c_int),
     "sph_step_adjoint": ([_CTX, C.c_double, C.c_int, _PP, _PP, _PP], C.c_int),
+    "sph_schur_local": ([C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP, _DP, _DP, _DP, C.POINTER(C.c_int), C.c_void_p],
+                        C.c_int),
+    "sph_schur_reduced": ([C.c_int, C.c_int, C.c_int, _DP, _DP, C.POINTER(C.c_int), C.c_void_p], C.c_int),
+    "sph_schur_back": ([C.c_int, C.c_int, _DP, _DP, _DP, _DP, _DP, _DP, C.c_void_p], C.c_int),
     "sph_adjoint_tape_use": ([_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "sph_strerror": ([C.c_int], C.c_char_p),
 }
@@ -95,6 +101,30 @@ def load(path: str = LIB):
             f.restype = res
         _lib = L
     return _lib
+
+
+def use_library(path: str):
+    """Switch every later call to the library at `path` (for example the
+    bounds-checked debug build, _build.LIB_CHECKED); returns the previous one.
+    Solvers created before the switch must be closed first."""
+    global _lib
+    prev = _lib
+    _lib = None
+    load(path)
+    return prev
+
+
+def restore_library(prev):
+    global _lib
+    _lib = prev
+
+
+def bounds_report():
+    """(violations since the last call, (field, i, j, k) of the first); -1 from a
+    regular build"""
+    first = (C.c_int * 4)()
+    n = load().sph_bounds_report(first)
+    return n, tuple(first)
 
 
 def _grid_struct(grid) -> sph_grid:
@@ -365,6 +395,10 @@ class Solver:
         """SPH_LINES_PARTITIONED (default), SPH_LINES_PARTITIONED_WARP (one warp per line) or
         SPH_LINES_THOMAS for the mixed-precision sweeps."""
         _check(load().sph_set_line_solver(self._h, int(which)), "sph_set_line_solver")
+
+    def set_tile(self, tj: int, ti: int):
+        """stencil tile shape: 128/(tj ti) phi points x tj theta rows x ti r rows"""
+        _check(load().sph_set_tile(self._h, int(tj), int(ti)), "sph_set_tile")
 
     KERNELS = ("avg", "coef", "rhs", "sweep_r", "sweep_theta", "sweep_phi")
 

@@ -172,17 +172,12 @@ __device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<
 }
 
 // The stencil kernels run on tiles of TK x TJ x TI points (phi fastest; 128
-// threads).  A block takes the fast path when its whole tile has its +-2
-// neighbourhood in r and theta inside the grid (a uniform choice).  On the
-// 128 x 256 x 256 workload the tile shape made no measurable difference
-// (128x1x1 to 16x4x2 all within 3 %), so the default is one phi row.
-#ifndef SPH_TILE_J
-#define SPH_TILE_J 1
-#endif
-#ifndef SPH_TILE_I
-#define SPH_TILE_I 1
-#endif
-constexpr int TILE_K = 128 / (SPH_TILE_J * SPH_TILE_I), TILE_J = SPH_TILE_J, TILE_I = SPH_TILE_I;
+// threads; the shape is set per context, sph_set_tile).  A block takes the
+// fast path when its whole tile has its +-2 neighbourhood in r and theta
+// inside the grid (a uniform choice).  On the 128 x 256 x 256 workload the
+// tile shape made no measurable difference (128x1x1 to 16x4x2 all within 3 %),
+// so the default is one phi row; the ensemble's autotuner picks it per grid
+// shape.
 template <typename G>
 __device__ __forceinline__ bool tile_inner(const G& g) {
   int i0 = blockIdx.z * blockDim.z, j0 = blockIdx.y * blockDim.y;
@@ -194,10 +189,14 @@ __device__ __forceinline__ bool tile_inner(const G& g) {
 // instantiations keep their registers.
 #define STENCIL_MINB(R) (sizeof(R) == 4 ? 16 : 1)
 
-static dim3 tile_grid(int nk, int nj, int ni) {
-  return dim3((nk + TILE_K - 1) / TILE_K, (nj + TILE_J - 1) / TILE_J, (ni + TILE_I - 1) / TILE_I);
+// grid of tiles of tj x ti rows of phi points (128 / (tj ti) each) over an
+// nk x nj x ni index box
+static dim3 tile_grid_of(int tj, int ti, int nk, int nj, int ni) {
+  int tk = 128 / (tj * ti);
+  return dim3((nk + tk - 1) / tk, (nj + tj - 1) / tj, (ni + ti - 1) / ti);
 }
-static const dim3 TILE_BLOCK(TILE_K, TILE_J, TILE_I);
+#define tile_grid(nk, nj, ni) tile_grid_of(c->tile_j, c->tile_i, nk, nj, ni)
+#define TILE_BLOCK dim3(128 / (c->tile_j * c->tile_i), c->tile_j, c->tile_i)
 
 // one block per tile
 template <typename R>
@@ -1053,6 +1052,7 @@ struct sph_ctx {
   cudaStream_t aux[3];   // side streams for independent launches of one stage
   cudaEvent_t efork, ejoin[3];
   int line_solver;       // SPH_LINES_* for the mixed path
+  int tile_j, tile_i;    // stencil tile: 128 / (tile_j tile_i) phi points x tile_j x tile_i
   size_t nscr;           // floats in each bulk scratch buffer
   // wall data (sph_set_bc): the mean of the t^n and t^{n+1} values of the 18
   // arrays (FP64, and FP32 in mixed mode) for the tangential ghosts, and the
@@ -1063,6 +1063,8 @@ struct sph_ctx {
   double* wmean64;
   float* wmean32;
   double* wnext;
+  double* wzero64;        // zeros of the largest wall size: the arrays without data
+  float* wzero32;
   // adjoint workspace (sph_step_adjoint), allocated on first use
   int adjK;               // iterates the workspace holds
   size_t fset;            // doubles of one 5-field set
@@ -1114,7 +1116,30 @@ extern "C" int sph_set_line_solver(sph_ctx* ctx, int which) {
   return SPH_OK;
 }
 
+extern "C" int sph_set_tile(sph_ctx* ctx, int tj, int ti) {
+  if (!ctx || tj < 1 || ti < 1 || tj * ti > 8 || (tj & (tj - 1)) || (ti & (ti - 1))) return SPH_ERR_ARG;
+  ctx->tile_j = tj;
+  ctx->tile_i = ti;
+  return SPH_OK;
+}
+
 extern "C" long long sph_launch_count(const sph_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int sph_bounds_report(int* first) {
+#ifdef SPH_CHECKED
+  int h[5] = {0, 0, 0, 0, 0}, z[5] = {0, 0, 0, 0, 0};
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(h, g_bounds, sizeof h) != cudaSuccess ||
+      cudaMemcpyToSymbol(g_bounds, z, sizeof z) != cudaSuccess)
+    return SPH_ERR_CUDA;
+  if (first)
+    for (int q = 0; q < 4; q++) first[q] = h[1 + q];
+  return h[0];
+#else
+  if (first)
+    for (int q = 0; q < 4; q++) first[q] = 0;
+  return -1;
+#endif
+}
 
 static void prof_free(sph_ctx* c) {
   for (int q = 0; q < c->evcap * 2; q++) cudaEventDestroy(c->ev[q]);
@@ -1141,6 +1166,7 @@ static void free_all(sph_ctx* c) {
   bufs_free(c->d32);
   cudaFree(c->bg); cudaFree(c->acc); cudaFree(c->flag);
   cudaFree(c->wmean64); cudaFree(c->wmean32); cudaFree(c->wnext);
+  cudaFree(c->wzero64); cudaFree(c->wzero32);
   cudaFree(c->adjS); cudaFree(c->adjW); cudaFree(c->adjC);
   cudaFree(c->tape_d); cudaFree(c->tape_ix); cudaFree(c->tape_li); cudaFree(c->tape_adj); cudaFree(c->adj_info);
   for (int f = 0; f < 5; f++) { cudaFree(c->U[0][f]); cudaFree(c->U[1][f]); cudaFree(c->src[f]); }
@@ -1275,6 +1301,14 @@ static int upload_background(sph_ctx* c, const double* pref, const double* Tref)
   return e;
 }
 
+// elements of wall array (component c, wall normal to d)
+static size_t wall_count(const Geo<double>& g, int c, int d) {
+  size_t nr = g.nr, nt = g.nt, np = g.np, npf = g.npf;
+  if (c == 0) return d == 1 ? (nr + 1) * np : d == 2 ? (nr + 1) * nt : nt * np;
+  if (c == 1) return d == 0 ? (nt + 1) * np : d == 2 ? nr * (nt + 1) : nr * np;
+  return d == 0 ? nt * npf : d == 1 ? nr * npf : nr * nt;
+}
+
 static int lines_prepare(const sph_ctx* c);
 static size_t lines_scratch(int nr, int nt, int np, int per);
 
@@ -1294,6 +1328,7 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   c->st = (cudaStream_t)stream;
   c->prec = pa->precision;
   c->line_solver = SPH_LINES_PARTITIONED;
+  c->tile_j = c->tile_i = 1;
   Geo<double> g;
   memset(&g, 0, sizeof g);
   g.nr = gr->nr; g.nt = gr->nth; g.np = gr->nph; g.per = gr->periodic_phi ? 1 : 0;
@@ -1359,6 +1394,23 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
   if (err != SPH_OK) { free_all(c); free(c); return err; }
   set_geo_ptrs(c->d64, g, c->bg, nr, nt);
   if (mixed) set_geo_ptrs(c->d32, g, c->bg, nr, nt);
+  {
+    // homogeneous walls: every wall array is the zero buffer
+    size_t wmax = 0;
+    for (int cc = 0; cc < 3; cc++)
+      for (int d = 0; d < 3; d++) {
+        size_t w = wall_count(g, cc, d);
+        if (w > wmax) wmax = w;
+      }
+    if (cudaMalloc((void**)&c->wzero64, wmax * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&c->wzero32, wmax * sizeof(float)) != cudaSuccess)
+      err = SPH_ERR_NOMEM;
+    else if (cudaMemset(c->wzero64, 0, wmax * sizeof(double)) != cudaSuccess ||
+             cudaMemset(c->wzero32, 0, wmax * sizeof(float)) != cudaSuccess)
+      err = SPH_ERR_CUDA;
+    for (int q = 0; q < 18; q++) { c->d64.g.w[q] = c->wzero64; c->d32.g.w[q] = c->wzero32; }
+    if (err) { cudaGetLastError(); free_all(c); free(c); return err; }
+  }
   // zero background
   double* zb = (double*)calloc(nr + 2, sizeof(double));
   double* tb = (double*)calloc(nr + 2, sizeof(double));
@@ -1428,14 +1480,6 @@ extern "C" int sph_set_iterate(sph_ctx* c, const double* const* fields, int on_d
   return e;
 }
 
-// elements of wall array (component c, wall normal to d)
-static size_t wall_count(const Geo<double>& g, int c, int d) {
-  size_t nr = g.nr, nt = g.nt, np = g.np, npf = g.npf;
-  if (c == 0) return d == 1 ? (nr + 1) * np : d == 2 ? (nr + 1) * nt : nt * np;
-  if (c == 1) return d == 0 ? (nt + 1) * np : d == 2 ? nr * (nt + 1) : nr * np;
-  return d == 0 ? nt * npf : d == 1 ? nr * npf : nr * nt;
-}
-
 extern "C" int sph_set_bc(sph_ctx* c, const double* const* wn, const double* const* wnp1, int on_device) {
   if (!c) return SPH_ERR_ARG;
   const Geo<double>& g = c->d64.g;
@@ -1450,10 +1494,11 @@ extern "C" int sph_set_bc(sph_ctx* c, const double* const* wn, const double* con
     c->woff[q] = tot;
     if (given) { tot += wall_count(g, cc, d); any = 1; }
   }
-  for (int q = 0; q < 18; q++) { c->d64.g.w[q] = NULL; c->d32.g.w[q] = NULL; }
+  for (int q = 0; q < 18; q++) { c->d64.g.w[q] = c->wzero64; c->d32.g.w[q] = c->wzero32; }
   c->d64.g.hasw = c->d32.g.hasw = 0;
   c->hasbc = 0;
   cudaFree(c->wmean64); cudaFree(c->wmean32); cudaFree(c->wnext);
+  cudaFree(c->wzero64); cudaFree(c->wzero32);
   cudaFree(c->adjS); cudaFree(c->adjW); cudaFree(c->adjC);
   cudaFree(c->tape_d); cudaFree(c->tape_ix); cudaFree(c->tape_li); cudaFree(c->tape_adj); cudaFree(c->adj_info);
   c->wmean64 = NULL; c->wmean32 = NULL; c->wnext = NULL;
@@ -2038,7 +2083,7 @@ extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* 
 
 // ------------------------------------------------------------ adjoint
 
-#define ADJ_TAPE_CAP 1536      // nodes per thread's tape
+#define ADJ_TAPE_CAP 512       // nodes per thread's tape (the longest location's rows record 370)
 #define ADJ_TAPE_BLOCKS 304    // blocks of 128 threads of the gradient kernels (two per SM)
 #define ADJ_FLAG_TAPE 8
 

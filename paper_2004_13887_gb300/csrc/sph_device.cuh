@@ -64,27 +64,24 @@ struct Geo {
   const T *rf2h, *rf2l, *sfh, *sfl;
   // Dirichlet wall data of Ubar for the tangential ghosts (ghost = 2 w - the
   // interior value): w[(c*3 + d)*2 + s] is velocity component c on the wall
-  // normal to direction d at side s, the mean of its t^n and t^{n+1} values
-  // (NULL entries are 0; hasw = 0 means homogeneous walls everywhere).
+  // normal to direction d at side s, the mean of its t^n and t^{n+1} values.
+  // Arrays without data point to a zero-filled buffer of the largest wall
+  // size, so a ghost is always one load (no flag, no null test).  hasw: whether
+  // any wall data are set (host bookkeeping).
   // Layouts: c = r: d = theta (nr+1)*np, d = phi (nr+1)*nt; c = theta:
   // d = r (nt+1)*np, d = phi nr*(nt+1); c = phi: d = r nt*npf, d = theta nr*npf.
   const T* w[18];
   int hasw;
 };
 
-// twice the wall value of component c on the wall normal to d at side s
-// (0 for homogeneous walls)
-// (c and d are constants at every call, so both candidate arrays are fixed
-// parameter slots and the side only selects between them: no dynamic index
-// into the kernel's parameters)
+// twice the wall value of component c on the wall normal to d at side s (c and
+// d are constants at every call, so both candidate arrays are fixed parameter
+// slots and the side only selects between them)
 template <typename G>
 __device__ __forceinline__ auto wall2(const G& g, int c, int d, int s, int idx) -> decltype(+*g.w[0]) {
   using V = decltype(+*g.w[0]);
-  if (!g.hasw) return V(0);
-  const auto* lo = g.w[(c * 3 + d) * 2];
-  const auto* hi = g.w[(c * 3 + d) * 2 + 1];
-  const auto* a = s ? hi : lo;
-  return a ? V(2) * a[idx] : V(0);
+  const auto* a = s ? g.w[(c * 3 + d) * 2 + 1] : g.w[(c * 3 + d) * 2];
+  return V(2) * a[idx];
 }
 
 struct Par {
@@ -192,10 +189,36 @@ template <typename R> struct MF { R* f[5]; };
 
 // 32-bit flat indices: the host refuses grids whose arrays (and line-solve
 // scratch) would not fit in an int.
-template <typename G> __device__ __forceinline__ int IC(const G& g, int i, int j, int k) { return (i * g.nt + j) * g.np + k; }
-template <typename G> __device__ __forceinline__ int IRf(const G& g, int i, int j, int k) { return (i * g.nt + j) * g.np + k; }
-template <typename G> __device__ __forceinline__ int ITf(const G& g, int i, int j, int k) { return (i * (g.nt + 1) + j) * g.np + k; }
-template <typename G> __device__ __forceinline__ int IPf(const G& g, int i, int j, int k) { return (i * g.nt + j) * g.npf + k; }
+//
+// Built with SPH_CHECKED (the bounds-checked debug library), every index is
+// checked against its field's extents first: a violation is counted in
+// g_bounds (with the first offending field and (i, j, k)) and the access is
+// redirected to element 0, so that the run goes on and the host reports it.
+#ifdef SPH_CHECKED
+__device__ int g_bounds[5];  // count, field, i, j, k of the first violation
+__device__ __forceinline__ int checked(int f, int i, int j, int k, int ni, int nj, int nk, int idx) {
+  if (i < 0 || i >= ni || j < 0 || j >= nj || k < 0 || k >= nk) {
+    if (atomicAdd(&g_bounds[0], 1) == 0) { g_bounds[1] = f; g_bounds[2] = i; g_bounds[3] = j; g_bounds[4] = k; }
+    return 0;
+  }
+  return idx;
+}
+#define SPH_IDX(f, ni, nj, nk, e) checked(f, i, j, k, ni, nj, nk, e)
+#else
+#define SPH_IDX(f, ni, nj, nk, e) (e)
+#endif
+template <typename G> __device__ __forceinline__ int IC(const G& g, int i, int j, int k) {
+  return SPH_IDX(0, g.nr, g.nt, g.np, (i * g.nt + j) * g.np + k);
+}
+template <typename G> __device__ __forceinline__ int IRf(const G& g, int i, int j, int k) {
+  return SPH_IDX(1, g.nr + 1, g.nt, g.np, (i * g.nt + j) * g.np + k);
+}
+template <typename G> __device__ __forceinline__ int ITf(const G& g, int i, int j, int k) {
+  return SPH_IDX(2, g.nr, g.nt + 1, g.np, (i * (g.nt + 1) + j) * g.np + k);
+}
+template <typename G> __device__ __forceinline__ int IPf(const G& g, int i, int j, int k) {
+  return SPH_IDX(3, g.nr, g.nt, g.npf, (i * g.nt + j) * g.npf + k);
+}
 
 // a / b; the mixed path uses the fast single-precision division (2 ulp)
 template <typename R> __device__ __forceinline__ R sdiv(R a, R b) { return a / b; }

@@ -12,6 +12,24 @@ def _partitioned_applies(grid) -> bool:
     return any(n in (16, 32, 48, 64, 128, 192, 256) for n in (grid.nr, grid.nt, grid.np)) or grid.np in (512, 1024)
 
 
+def partition(points, world: int):
+    """Split instances of the given sizes (grid points) over `world` ranks,
+    balanced by points: largest first, each to the rank with the fewest points
+    so far (ties to the lower rank).  Returns one sorted list of instance
+    indices per rank; every index appears exactly once.  The instances are
+    independent, so each rank steps its share alone -- no data-path
+    collective."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for q in sorted(range(len(points)), key=lambda q: (-points[q], q)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        parts[r].append(q)
+        load[r] += points[q]
+    return [sorted(p) for p in parts]
+
+
 def time_steps(solver, dt, n_iter, steps=2, warmup=1):
     """milliseconds per step on the solver's stream (CUDA events)"""
     import torch
@@ -26,30 +44,43 @@ def time_steps(solver, dt, n_iter, steps=2, warmup=1):
     return e0.elapsed_time(e1) / steps
 
 
-def autotune(cases, dt, n_iter):
-    """For every distinct grid shape among the cases, the faster line solver of
-    the mixed mode (partitioned or block Thomas), timed on a scratch solver
-    started from that shape's first case.  Returns {shape: SPH_LINES_*}."""
+TILES = ((1, 1), (2, 1), (4, 1), (2, 2), (8, 1), (4, 2))
+
+
+def autotune(cases, dt, n_iter, tiles=TILES):
+    """For every distinct grid shape among the cases: the fastest line solver of
+    the mixed mode (partitioned, partitioned with a warp per line, or block
+    Thomas), then with it the fastest stencil tile shape among `tiles`, each
+    timed on one scratch solver started from that shape's first case.
+    Returns {shape: (SPH_LINES_*, (tj, ti))}."""
     import torch
     choice = {}
     for c in cases:
         shape = (c.grid.nr, c.grid.nt, c.grid.np)
         if shape in choice:
             continue
-        if not _partitioned_applies(c.grid):
-            choice[shape] = SPH_LINES_THOMAS
-            continue
+        s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
+        s.set_background(*c.bg)
+        init = [torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init]
+        solvers = (SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS) \
+            if _partitioned_applies(c.grid) else (SPH_LINES_THOMAS,)
         best, best_ms = None, None
-        for which in (SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS):
-            s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
-            s.set_background(*c.bg)
-            s.set_state([torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init])
+        for which in solvers:
+            s.set_state(init)
             s.set_line_solver(which)
             ms = time_steps(s, dt, n_iter)
-            s.close()
             if best_ms is None or ms < best_ms:
                 best, best_ms = which, ms
-        choice[shape] = best
+        s.set_line_solver(best)
+        tile, tile_ms = tiles[0], None
+        for tj, ti in tiles:
+            s.set_state(init)
+            s.set_tile(tj, ti)
+            ms = time_steps(s, dt, n_iter)
+            if tile_ms is None or ms < tile_ms:
+                tile, tile_ms = (tj, ti), ms
+        s.close()
+        choice[shape] = (best, tile)
     return choice
 
 
@@ -70,7 +101,9 @@ class Ensemble:
             s.set_state([torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init])
             shape = (c.grid.nr, c.grid.nt, c.grid.np)
             if shape in self.choice:
-                s.set_line_solver(self.choice[shape])
+                which, (tj, ti) = self.choice[shape]
+                s.set_line_solver(which)
+                s.set_tile(tj, ti)
             self.solvers.append(s)
         torch.cuda.synchronize()
         self.batch = Batch(self.solvers)

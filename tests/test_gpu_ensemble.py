@@ -104,8 +104,8 @@ def test_autotune_choices_agree():
     cs = _cases()
     choice = ensemble.autotune(cs, 1.0, 2)
     assert set(choice) == {(c.grid.nr, c.grid.nt, c.grid.np) for c in cs}
-    assert all(v in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP)
-               for v in choice.values())
+    assert all(v[0] in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP)
+               and v[1] in ensemble.TILES for v in choice.values())
     c = cs[5]   # 64 x 64 x 128: both solvers apply
     xs = []
     for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP):
@@ -119,6 +119,30 @@ def test_autotune_choices_agree():
         scale = float(np.max(np.abs(xs[0][f] - c.init[f]))) or 1.0
         for x in xs[1:]:
             assert float(np.max(np.abs(xs[0][f] - x[f]))) <= 1e-5 * scale
+
+
+def test_tile_shape_leaves_results_unchanged():
+    """The stencil tile shape the autotuner picks changes how the kernels are
+    launched, not what they compute: every shape gives bit-for-bit the same
+    step."""
+    c = _cases()[3]   # 48 x 64 x 64: boundary and interior tiles in r and theta
+    ref = None
+    for tj, ti in ensemble.TILES:
+        s = _solver(c)
+        s.set_tile(tj, ti)
+        s.step(c.dt, 2)
+        got = to_host(s.get_state())
+        s.close()
+        if ref is None:
+            ref = got
+        for f in range(5):
+            assert np.array_equal(got[f], ref[f]), ((tj, ti), f)
+    s = _solver(c)
+    with pytest.raises(sph.SphError):
+        s.set_tile(3, 1)
+    with pytest.raises(sph.SphError):
+        s.set_tile(4, 4)
+    s.close()
 
 
 def test_ensemble_of_config_five():
