@@ -146,7 +146,7 @@ int sph_status(sph_ctx* ctx, double* residual_out);
  * iteration the transposed line solves (phi, theta, r) and the gradient over
  * Ubar of the right-hand side and of the three line operators, by reverse-mode
  * differentiation of the library's own row functions.  Work buffers (about 16
- * fields plus 17 coefficient planes and 0.7 GB of per-thread tapes) are
+ * fields plus 17 coefficient planes and 1.4 GB of per-thread tapes) are
  * allocated on the first call and kept with the context.  Synchronises.
  * Errors: SPH_ERR_ARG, SPH_ERR_NOMEM, SPH_ERR_CUDA, SPH_ERR_SINGULAR (a zero pivot
  * in a transposed solve), SPH_ERR_TAPE (a location's rows outgrew the tape). */

@@ -130,7 +130,7 @@ __global__ void k_cvt_in(long n, const double* __restrict__ a, R* __restrict__ o
 
 // The coefficients of centre (i, j, k) (flat index t) into c: the planes of a
 // Coef (k_coef), or the adjoint's slots for the same values.
-template <bool CIJ, typename R, typename Out>
+template <int CIJ, typename R, typename Out>
 __device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<R>& ub, const Out& c, int i, int j,
                                         int k, int t) {
   const auto UR = ub.f[1];
@@ -199,15 +199,15 @@ static dim3 tile_grid_of(int tj, int ti, int nk, int nj, int ni) {
 #define TILE_BLOCK dim3(128 / (c->tile_j * c->tile_i), c->tile_j, c->tile_i)
 
 // one block per tile
-template <typename R>
+template <typename R, bool W>
 __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_coef(Geo<R> g, Par P, CF<R> ub, Coef<R> c) {
   int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
       i = blockIdx.z * blockDim.z + threadIdx.z;
-  bool inner = tile_inner(g);
+  bool inner = tile_inner(g) && !g.hasw;  // with wall data every tile takes the checked path
   if (k >= g.np || j >= g.nt || i >= g.nr) return;
   int t = IC(g, i, j, k);
-  if (inner) coef_at<false>(g, P, ub, c, i, j, k, t);
-  else coef_at<true>(g, P, ub, c, i, j, k, t);
+  if (inner) coef_at<0>(g, P, ub, c, i, j, k, t);
+  else coef_at<W ? 2 : 1>(g, P, ub, c, i, j, k, t);
 }
 
 // div(Ubar) at centre (i,j,k), in FP64 from U^n and U^k (Ubar = (U^n+U^k)/2).
@@ -276,7 +276,7 @@ __device__ __forceinline__ R div_ubar_of(const Geo<R>& g, const CF<R>& ub, int i
 // R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per
 // centre; written to Rout.f[0][t], Rout.f[4][t] (a field pair, or the adjoint's
 // slots).
-template <bool CIJ, typename R, typename Out>
+template <int CIJ, typename R, typename Out>
 __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd, const Par& P, const Coef<R>& c,
                                          const CF<R>& ub, const CF<R>& ul, const CF<double>& un, const CF<double>& uk,
                                          const CF<R>& D, int hasD, const CF<double>& src, int has_src, R tau,
@@ -336,22 +336,22 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
 }
 
 // one block per tile
-template <typename R>
+template <typename R, bool W>
 __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
                                                CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
                                                int has_src, R tau, MF<R> Rout) {
   int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
       i = blockIdx.z * blockDim.z + threadIdx.z;
-  bool inner = tile_inner(g);
+  bool inner = tile_inner(g) && !g.hasw;  // with wall data every tile takes the checked path
   if (k >= g.np || j >= g.nt || i >= g.nr) return;
   int t = IC(g, i, j, k);
-  if (inner) rhs_c_at<false>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
-  else rhs_c_at<true>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+  if (inner) rhs_c_at<0>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+  else rhs_c_at<W ? 2 : 1>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
 }
 
 // R for the momentum row of component D on its faces: one thread per face
 // (zero on wall faces, which are not unknowns); written to Rout.f[1 + D][t].
-template <bool CIJ, int D, typename R, typename Out>
+template <int CIJ, int D, typename R, typename Out>
 __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub,
                                          const CF<R>& Dv, int hasD, const CF<double>& src, int has_src, R tau,
                                          const Out& Rout, int i, int j, int k, int t) {
@@ -453,19 +453,19 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
 }
 
 // one block per tile of faces; zero on wall faces, which are not unknowns
-template <typename R, int D>
+template <typename R, int D, bool W>
 __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<R> Dv, int hasD,
                                                CF<double> src, int has_src, R tau, MF<R> Rout) {
   int nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
   int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
       i = blockIdx.z * blockDim.z + threadIdx.z;
-  bool inner = tile_inner(g);
+  bool inner = tile_inner(g) && !g.hasw;  // with wall data every tile takes the checked path
   if (k >= nk || j >= nj || i >= g.nr + (D == 0)) return;
   int t = (i * nj + j) * nk + k;
   bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
   if (wall) { Rout.f[1 + D][t] = R(0); return; }
-  if (inner) rhs_u_at<false, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
-  else rhs_u_at<true, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+  if (inner) rhs_u_at<0, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+  else rhs_u_at<W ? 2 : 1, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
 }
 
 // ------------------------------------------------------------ line solvers
@@ -1498,9 +1498,6 @@ extern "C" int sph_set_bc(sph_ctx* c, const double* const* wn, const double* con
   c->d64.g.hasw = c->d32.g.hasw = 0;
   c->hasbc = 0;
   cudaFree(c->wmean64); cudaFree(c->wmean32); cudaFree(c->wnext);
-  cudaFree(c->wzero64); cudaFree(c->wzero32);
-  cudaFree(c->adjS); cudaFree(c->adjW); cudaFree(c->adjC);
-  cudaFree(c->tape_d); cudaFree(c->tape_ix); cudaFree(c->tape_li); cudaFree(c->tape_adj); cudaFree(c->adj_info);
   c->wmean64 = NULL; c->wmean32 = NULL; c->wnext = NULL;
   c->wtot = tot;
   if (!any) return SPH_OK;
@@ -1657,7 +1654,8 @@ static int prepare(sph_ctx* c, Bufs<R>& b, int have_iter, CF<R>* ub_out, double*
   }
   k_begin(c, SPH_K_COEF);
   const Geo<double>& gg = c->d64.g;
-  k_coef<R><<<tile_grid(gg.np, gg.nt, gg.nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, ub, b.c);
+  if (b.g.hasw) k_coef<R, true><<<tile_grid(gg.np, gg.nt, gg.nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, ub, b.c);
+  else k_coef<R, false><<<tile_grid(gg.np, gg.nt, gg.nr), TILE_BLOCK, 0, c->st>>>(b.g, c->P, ub, b.c);
   if (launch_ok(c)) return SPH_ERR_CUDA;
   *ub_out = ub;
   return SPH_OK;
@@ -1694,11 +1692,25 @@ static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, do
   if (fork_aux(c, 3)) return SPH_ERR_CUDA;
   const Geo<double>& gg = c->d64.g;
   int nr = gg.nr, nt = gg.nt, np = gg.np, npf = gg.npf;
-  k_rhs_c<R><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv, hasD, src,
-                                                                has_src, tr, Rout);
-  k_rhs_u<R, 0><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->aux[0]>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 1><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->aux[1]>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
-  k_rhs_u<R, 2><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->aux[2]>>>(b.g, c->P, b.c, ub, Dv, hasD, src, has_src, tr, Rout);
+  if (b.g.hasw) {
+    k_rhs_c<R, true><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv,
+                                                                      hasD, src, has_src, tr, Rout);
+    k_rhs_u<R, 0, true><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->aux[0]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
+                                                                                 has_src, tr, Rout);
+    k_rhs_u<R, 1, true><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->aux[1]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
+                                                                                 has_src, tr, Rout);
+    k_rhs_u<R, 2, true><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->aux[2]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
+                                                                              has_src, tr, Rout);
+  } else {
+    k_rhs_c<R, false><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv,
+                                                                       hasD, src, has_src, tr, Rout);
+    k_rhs_u<R, 0, false><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->aux[0]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
+                                                                                  has_src, tr, Rout);
+    k_rhs_u<R, 1, false><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->aux[1]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
+                                                                                  has_src, tr, Rout);
+    k_rhs_u<R, 2, false><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->aux[2]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
+                                                                               has_src, tr, Rout);
+  }
   if (join_aux(c, 3)) return SPH_ERR_CUDA;
   c->launches += 3;  // launch_ok counts the fourth
   return launch_ok(c);
@@ -2084,7 +2096,7 @@ extern "C" int sph_step(sph_ctx* c, double dt, int n_iter, const double* const* 
 // ------------------------------------------------------------ adjoint
 
 #define ADJ_TAPE_CAP 512       // nodes per thread's tape (the longest location's rows record 370)
-#define ADJ_TAPE_BLOCKS 304    // blocks of 128 threads of the gradient kernels (two per SM)
+#define ADJ_TAPE_BLOCKS 608    // blocks of 128 threads of the gradient kernels (four per SM: their registers allow it)
 #define ADJ_FLAG_TAPE 8
 
 static int adj_alloc(sph_ctx* c, int K) {
@@ -2092,8 +2104,10 @@ static int adj_alloc(sph_ctx* c, int K) {
   cudaFree(c->adjS);
   c->adjS = NULL;
   c->adjK = 0;
+  // every field of a set starts on a 256-byte boundary: the averaging kernel
+  // reads the state in 16-byte pairs, and aligned rows keep the loads whole
   size_t fs = 0;
-  for (int f = 0; f < 5; f++) { c->foff[f] = fs; fs += c->nf[f]; }
+  for (int f = 0; f < 5; f++) { c->foff[f] = fs; fs += (c->nf[f] + 31) / 32 * 32; }
   c->fset = fs;
   if (cudaMalloc((void**)&c->adjS, (size_t)K * fs * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return SPH_ERR_NOMEM; }
   c->adjK = K;

@@ -236,16 +236,16 @@ __global__ void __launch_bounds__(128) k_adj_rhs(AdjArgs A, int kind) {
     RowsOut out;
     ad psi;
     if (kind == 0) {
-      rhs_c_at<true>(ga, g, A.P, c, ub, none, noned, noned, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
+      rhs_c_at<2>(ga, g, A.P, c, ub, none, noned, noned, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
       psi = out.f[0].v * w0 + out.f[4].v * w4;
     } else if (kind == 1) {
-      rhs_u_at<true, 0>(ga, A.P, c, ub, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
+      rhs_u_at<2, 0>(ga, A.P, c, ub, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
       psi = out.f[1].v * w0;
     } else if (kind == 2) {
-      rhs_u_at<true, 1>(ga, A.P, c, ub, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
+      rhs_u_at<2, 1>(ga, A.P, c, ub, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
       psi = out.f[2].v * w0;
     } else {
-      rhs_u_at<true, 2>(ga, A.P, c, ub, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
+      rhs_u_at<2, 2>(ga, A.P, c, ub, none, 0, noned, 0, ad(A.tau), out, i, j, k, t);
       psi = out.f[3].v * w0;
     }
     finish(A, T, psi);
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(128) k_adj_coef(AdjArgs A) {
     T.n = 0;
     CF<ad> ub = leaves_ub(A, &T);
     CoefOut o;
-    coef_at<true>(ga, A.P, ub, o, i, j, k, t);
+    coef_at<2>(ga, A.P, ub, o, i, j, k, t);
     const Slot* sl[NCOEF] = {&o.Pb, &o.Tb, &o.rho, &o.drho, &o.beta, &o.uc0, &o.uc1, &o.uc2,
                              &o.grr, &o.gtt, &o.gpp, &o.srt, &o.srp, &o.stp, &o.dvr, &o.dvt, &o.dvp};
     ad psi;

@@ -77,12 +77,19 @@ struct Geo {
 // twice the wall value of component c on the wall normal to d at side s (c and
 // d are constants at every call, so both candidate arrays are fixed parameter
 // slots and the side only selects between them)
+// (out of line: ghosts are a few threads' business, and inlined into every
+// accessor the wall loads would take registers from the stencils' hot path)
+template <typename T>
+__device__ __noinline__ T wall2_load(const T* lo, const T* hi, int s, int idx) {
+  return T(2) * (s ? hi : lo)[idx];
+}
 template <typename G>
 __device__ __forceinline__ auto wall2(const G& g, int c, int d, int s, int idx) -> decltype(+*g.w[0]) {
-  using V = decltype(+*g.w[0]);
-  const auto* a = s ? g.w[(c * 3 + d) * 2 + 1] : g.w[(c * 3 + d) * 2];
-  return V(2) * a[idx];
+  return wall2_load(g.w[(c * 3 + d) * 2], g.w[(c * 3 + d) * 2 + 1], s, idx);
 }
+// the wall term of a ghost on the checked paths: read only when the kernel was
+// instantiated for wall data (CIJ == 2), compiled out otherwise (CIJ == 1)
+#define WALL2(...) (CIJ == 2 ? wall2(g, __VA_ARGS__) : decltype(wall2(g, __VA_ARGS__))(0))
 
 struct Par {
   double gamma, cv, Pr, mu, pinf, g, omega;
@@ -228,59 +235,65 @@ template <typename G> __device__ __forceinline__ int wrapk(const G& g, int k) { 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ---------------------------------------------------------------- accessors
-// CIJ = false skips the checks on i and j: for points whose +-2 neighbourhood in
+// CIJ = 0 skips the checks on i and j: for points whose +-2 neighbourhood in
 // r and theta is inside the grid (the kernels decide this per block, so warps
 // do not diverge); k (phi) is always checked.
 //
 // Centre perturbation with zero Neumann ghosts (the background has its own).
 template <typename P> using ValOf = typename std::decay<decltype(std::declval<P>()[0])>::type;
 
-template <bool CIJ = true, typename G, typename P>
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> cpert(const G& g, const P& f, int i, int j, int k) {
   int ii = CIJ ? clampi(i, 0, g.nr - 1) : i, jj = CIJ ? clampi(j, 0, g.nt - 1) : j;
   int kk = g.per ? wrapk(g, k) : clampi(k, 0, g.np - 1);
   return f[IC(g, ii, jj, kk)];
 }
 // Velocities with Dirichlet ghosts on tangential walls: ghost = 2 w - interior
-// (w = 0, no-slip, unless wall data were set).
-template <bool CIJ = true, typename G, typename P>
+// (w = 0, no-slip, unless wall data were set).  CIJ = 0: interior points, no
+// checks on i and j and the homogeneous rule for the phi walls; 1: checked,
+// homogeneous walls; 2: checked, wall data read (the kernels send every tile
+// to 2 when wall data are set and are instantiated without it otherwise, so
+// the other paths carry no wall code).
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> vr(const G& g, const P& u, int i, int j, int k) {
-  if (CIJ && j < 0) return wall2(g, 0, 1, 0, i * g.np + k) - u[IRf(g, i, 0, k)];
-  if (CIJ && j >= g.nt) return wall2(g, 0, 1, 1, i * g.np + k) - u[IRf(g, i, g.nt - 1, k)];
+  if (CIJ && j < 0) return WALL2(0, 1, 0, i * g.np + k) - u[IRf(g, i, 0, k)];
+  if (CIJ && j >= g.nt) return WALL2(0, 1, 1, i * g.np + k) - u[IRf(g, i, g.nt - 1, k)];
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
-    else return wall2(g, 0, 2, k >= g.np, i * g.nt + j) - u[IRf(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else if constexpr (CIJ != 0) return WALL2(0, 2, k >= g.np, i * g.nt + j) - u[IRf(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else return -u[IRf(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return u[IRf(g, i, j, k)];
 }
-template <bool CIJ = true, typename G, typename P>
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> vt(const G& g, const P& u, int i, int j, int k) {
-  if (CIJ && i < 0) return wall2(g, 1, 0, 0, j * g.np + k) - u[ITf(g, 0, j, k)];
-  if (CIJ && i >= g.nr) return wall2(g, 1, 0, 1, j * g.np + k) - u[ITf(g, g.nr - 1, j, k)];
+  if (CIJ && i < 0) return WALL2(1, 0, 0, j * g.np + k) - u[ITf(g, 0, j, k)];
+  if (CIJ && i >= g.nr) return WALL2(1, 0, 1, j * g.np + k) - u[ITf(g, g.nr - 1, j, k)];
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
-    else return wall2(g, 1, 2, k >= g.np, i * (g.nt + 1) + j) - u[ITf(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else if constexpr (CIJ != 0) return WALL2(1, 2, k >= g.np, i * (g.nt + 1) + j) - u[ITf(g, i, j, k < 0 ? 0 : g.np - 1)];
+    else return -u[ITf(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return u[ITf(g, i, j, k)];
 }
-template <bool CIJ = true, typename G, typename P>
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> vp(const G& g, const P& u, int i, int j, int k) {
   if (g.per) k = wrapk(g, k);
-  if (CIJ && i < 0) return wall2(g, 2, 0, 0, j * g.npf + k) - u[IPf(g, 0, j, k)];
-  if (CIJ && i >= g.nr) return wall2(g, 2, 0, 1, j * g.npf + k) - u[IPf(g, g.nr - 1, j, k)];
-  if (CIJ && j < 0) return wall2(g, 2, 1, 0, i * g.npf + k) - u[IPf(g, i, 0, k)];
-  if (CIJ && j >= g.nt) return wall2(g, 2, 1, 1, i * g.npf + k) - u[IPf(g, i, g.nt - 1, k)];
+  if (CIJ && i < 0) return WALL2(2, 0, 0, j * g.npf + k) - u[IPf(g, 0, j, k)];
+  if (CIJ && i >= g.nr) return WALL2(2, 0, 1, j * g.npf + k) - u[IPf(g, g.nr - 1, j, k)];
+  if (CIJ && j < 0) return WALL2(2, 1, 0, i * g.npf + k) - u[IPf(g, i, 0, k)];
+  if (CIJ && j >= g.nt) return WALL2(2, 1, 1, i * g.npf + k) - u[IPf(g, i, g.nt - 1, k)];
   return u[IPf(g, i, j, k)];
 }
-template <bool CIJ = true, typename G, typename P>
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> hr(const G& g, const P& u, int i, int j, int k) {
   return ValOf<P>(0.5) * (vr<CIJ>(g, u, i, j, k) + vr<CIJ>(g, u, i + 1, j, k));
 }
-template <bool CIJ = true, typename G, typename P>
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> ht(const G& g, const P& u, int i, int j, int k) {
   return ValOf<P>(0.5) * (vt<CIJ>(g, u, i, j, k) + vt<CIJ>(g, u, i, j + 1, k));
 }
-template <bool CIJ = true, typename G, typename P>
+template <int CIJ = 2, typename G, typename P>
 __device__ __forceinline__ ValOf<P> hp(const G& g, const P& u, int i, int j, int k) {
   return ValOf<P>(0.5) * (vp<CIJ>(g, u, i, j, k) + vp<CIJ>(g, u, i, j, k + 1));
 }
@@ -291,37 +304,32 @@ __device__ __forceinline__ R rho_at(const Geo<R>& g, const Coef<R>& c, int i, in
 }
 
 // A velocity component averaged to centre (i, j, k): in interior blocks
-// (CIJ = false) read from the coefficient plane k_coef wrote (uc0/uc1/uc2, the
-// same FP32 operations, so the same value), with the Dirichlet ghost -- the
-// two faces' 2 w minus the mirrored centre -- beyond a phi wall and the
-// periodic wrap (only used for the components tangential to phi, CC = 0 or 1);
+// (CIJ = 0) read from the coefficient plane k_coef wrote (uc0/uc1/uc2, the
+// same FP32 operations, so the same value), with the no-slip ghost -- minus the
+// mirrored centre -- beyond a phi wall (interior blocks run only without wall
+// data) and the periodic wrap (only used for the components tangential to phi);
 // elsewhere the face average with all checks.
 template <int CC, typename R>
 __device__ __forceinline__ R ucen(const Geo<R>& g, const typename Val<R>::CP& plane, int i, int j, int k) {
   if (k < 0 || k >= g.np) {
     if (g.per) k = wrapk(g, k);
-    else {
-      int s = k >= g.np, kk = s ? g.np - 1 : 0;
-      R w = CC == 0 ? R(0.5) * (wall2(g, 0, 2, s, i * g.nt + j) + wall2(g, 0, 2, s, (i + 1) * g.nt + j))
-                    : R(0.5) * (wall2(g, 1, 2, s, i * (g.nt + 1) + j) + wall2(g, 1, 2, s, i * (g.nt + 1) + j + 1));
-      return w - plane[IC(g, i, j, kk)];
-    }
+    else return -plane[IC(g, i, j, k < 0 ? 0 : g.np - 1)];
   }
   return plane[IC(g, i, j, k)];
 }
-template <bool CIJ, typename R, typename P>
+template <int CIJ, typename R, typename P>
 __device__ __forceinline__ R hrc(const Geo<R>& g, const Coef<R>& c, const P& u, int i, int j, int k) {
-  if constexpr (CIJ) return hr<true>(g, u, i, j, k);
+  if constexpr (CIJ != 0) return hr<CIJ>(g, u, i, j, k);
   else return ucen<0>(g, c.uc0, i, j, k);
 }
-template <bool CIJ, typename R, typename P>
+template <int CIJ, typename R, typename P>
 __device__ __forceinline__ R htc(const Geo<R>& g, const Coef<R>& c, const P& u, int i, int j, int k) {
-  if constexpr (CIJ) return ht<true>(g, u, i, j, k);
+  if constexpr (CIJ != 0) return ht<CIJ>(g, u, i, j, k);
   else return ucen<1>(g, c.uc1, i, j, k);
 }
-template <bool CIJ, typename R, typename P>
+template <int CIJ, typename R, typename P>
 __device__ __forceinline__ R hpc(const Geo<R>& g, const Coef<R>& c, const P& u, int i, int j, int k) {
-  if constexpr (CIJ) return hp<true>(g, u, i, j, k);
+  if constexpr (CIJ != 0) return hp<CIJ>(g, u, i, j, k);
   else return ucen<2>(g, c.uc2, i, j, k);
 }
 
@@ -519,7 +527,7 @@ __device__ __forceinline__ void row_f(const Geo<R>& g, const Par& P, const Coef<
 template <typename R>
 struct SPt { R rho0, rho1, ua; };
 
-template <bool CIJ = true, typename R>
+template <int CIJ = 2, typename R>
 __device__ __forceinline__ SPt<R> load_s(const Geo<R>& g, const Coef<R>& c, const CF<R>& ub, int cc, int d, int i,
                                          int j, int k) {
   SPt<R> q;
@@ -557,7 +565,7 @@ __device__ __forceinline__ void row_sw(const Geo<R>& g, const Par& P, const SPt<
   }
 }
 
-template <bool CIJ = true, typename R>
+template <int CIJ = 2, typename R>
 __device__ __forceinline__ void row_s(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub, int cc, int d,
                                       int i, int j, int k, R w[3]) {
   row_sw(g, P, load_s<CIJ>(g, c, ub, cc, d, i, j, k), cc, d, i, j, w);

@@ -306,7 +306,7 @@ __device__ __forceinline__ void stage_block(const SweepArgs<float>& S, float* sm
 // branches would crowd the 48-register budget of the scalar kernels
 template <int D, int KIND>
 __device__ __noinline__ SPt<float> stage_scalar_edge(const SweepArgs<float>& S, int i, int j, int k) {
-  return load_s<true>(S.g, S.c, S.ub, trans_comp(D, KIND), D, i, j, k);
+  return load_s<2>(S.g, S.c, S.ub, trans_comp(D, KIND), D, i, j, k);
 }
 
 template <int D, int KIND, int FS>

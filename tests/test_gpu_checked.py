@@ -32,6 +32,8 @@ def _cases():
     out.append(("sector", c.grid, c.par, c.bg, c.init, c.source(0.5 * c.dt), c.dt))
     c = cases.bubble((6, 7, 8), seed=2, dt=1.0)
     out.append(("bubble", c.grid, c.par, c.bg, c.init, None, c.dt))
+    c = cases.sector_mms((3, 5, 7))   # odd field sizes: sub-buffers at odd offsets would misalign pair loads
+    out.append(("ragged", c.grid, c.par, c.bg, c.init, c.source(0.5 * c.dt), c.dt))
     c = cases.bubble((8, 16, 16), seed=2, dt=1.0)
     out.append(("bubble16", c.grid, c.par, c.bg, c.init, None, c.dt))
     par = Params(gamma=1.4, cv=2.5, Pr=0.7, mu=0.05, pinf=2.0, g=0.3, omega=0.4)
