@@ -468,7 +468,7 @@ def run_ensemble(args, rank, world, dist):
                                    "radius 1-3 km, K=2, dt=1 s, one CUDA graph per two steps",
                        "instances": len(specs), "instances_rank0": len(cs), "points": total_pts,
                        "points_rank0": pts, "shapes": shapes,
-                       "line_solver": {f"{k[0]}x{k[1]}x{k[2]}": ({0: "thomas", 1: "partitioned", 2: "partitioned_warp"}[v[0]])
+                       "line_solver": {f"{k[0]}x{k[1]}x{k[2]}": ({0: "thomas", 1: "partitioned", 2: "partitioned_warp", 3: "partitioned_narrow"}[v[0]])
                                        for k, v in ens.choice.items()},
                        "tile": {f"{k[0]}x{k[1]}x{k[2]}": f"{128 // (v[1][0] * v[1][1])}x{v[1][0]}x{v[1][1]}"
                                 for k, v in ens.choice.items()},

@@ -198,7 +198,11 @@ int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double
  * (chunks of 6 and 8), phi lines of 512 and 1024 take 64 and 128 lanes (2 and
  * 4 warps, chunks of 8); other lines use the block Thomas path.
  * SPH_LINES_PARTITIONED_WARP: the same with 32 lanes (one line per warp) for
- * the lines of 64 and 128 cells.  SPH_LINES_THOMAS: block (and scalar) Thomas, one thread per
+ * the lines of 64 and 128 cells.  SPH_LINES_PARTITIONED_NARROW: fewer lanes and
+ * longer chunks for the short lines -- 4 lanes with chunks of 4 for lines of
+ * 16 cells, 8 lanes with chunks of 4, 6 and 8 for lines of 32, 48 and 64 --
+ * so that less of the work is in the reduction; other lengths as
+ * SPH_LINES_PARTITIONED.  SPH_LINES_THOMAS: block (and scalar) Thomas, one thread per
  * line, with the Woodbury / Sherman-Morrison correction on cyclic lines.  All
  * give the exact solution up to rounding (no pivoting between blocks in any).
  * The FP64 mode always uses block Thomas.  Returns SPH_ERR_ARG for other
@@ -206,6 +210,7 @@ int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double
 #define SPH_LINES_THOMAS 0
 #define SPH_LINES_PARTITIONED 1
 #define SPH_LINES_PARTITIONED_WARP 2
+#define SPH_LINES_PARTITIONED_NARROW 3
 int sph_set_line_solver(sph_ctx* ctx, int which);
 
 /* Tile shape of the stencil kernels (coefficients, right-hand side): blocks of

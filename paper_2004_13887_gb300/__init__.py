@@ -17,13 +17,15 @@ import numpy as np
 from ._build import LIB, build
 
 __all__ = ["build", "load", "Solver", "Batch", "SphError", "sph_field_size", "SPH_PREC_FP64", "SPH_PREC_MIXED",
-           "SPH_LINES_THOMAS", "SPH_LINES_PARTITIONED", "SPH_LINES_PARTITIONED_WARP"]
+           "SPH_LINES_THOMAS", "SPH_LINES_PARTITIONED", "SPH_LINES_PARTITIONED_WARP",
+           "SPH_LINES_PARTITIONED_NARROW"]
 
 SPH_PREC_FP64 = 0
 SPH_PREC_MIXED = 1
 SPH_LINES_THOMAS = 0
 SPH_LINES_PARTITIONED = 1
 SPH_LINES_PARTITIONED_WARP = 2
+SPH_LINES_PARTITIONED_NARROW = 3
 
 _ERRORS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "non-finite state",
            -4: "zero pivot in a line solve", -5: "device allocation failed", -6: "adjoint tape too short"}
@@ -392,7 +394,8 @@ class Solver:
         return out
 
     def set_line_solver(self, which: int):
-        """SPH_LINES_PARTITIONED (default), SPH_LINES_PARTITIONED_WARP (one warp per line) or
+        """SPH_LINES_PARTITIONED (default), SPH_LINES_PARTITIONED_WARP (one warp per line),
+        SPH_LINES_PARTITIONED_NARROW (4 or 8 lanes for lines of 16 to 64 cells) or
         SPH_LINES_THOMAS for the mixed-precision sweeps."""
         _check(load().sph_set_line_solver(self._h, int(which)), "sph_set_line_solver")
 

@@ -5,11 +5,28 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS, SPH_PREC_MIXED, Batch, Solver
+from . import (SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_NARROW, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS,
+               SPH_PREC_MIXED, Batch, Solver)
 
 
 def _partitioned_applies(grid) -> bool:
     return any(n in (16, 32, 48, 64, 128, 192, 256) for n in (grid.nr, grid.nt, grid.np)) or grid.np in (512, 1024)
+
+
+def _candidates(grid):
+    """the line solvers worth timing on a grid: the narrow layout only where a
+    direction has lines of 16 to 64 cells, the one-warp layout only where one
+    has 64 or 128"""
+    if not _partitioned_applies(grid):
+        return (SPH_LINES_THOMAS,)
+    ns = (grid.nr, grid.nt, grid.np)
+    out = [SPH_LINES_PARTITIONED]
+    if any(n in (64, 128) for n in ns):
+        out.append(SPH_LINES_PARTITIONED_WARP)
+    if any(n in (16, 32, 48, 64) for n in ns):
+        out.append(SPH_LINES_PARTITIONED_NARROW)
+    out.append(SPH_LINES_THOMAS)
+    return tuple(out)
 
 
 def partition(points, world: int):
@@ -49,8 +66,8 @@ TILES = ((1, 1), (2, 1), (4, 1), (2, 2), (8, 1), (4, 2))
 
 def autotune(cases, dt, n_iter, tiles=TILES):
     """For every distinct grid shape among the cases: the fastest line solver of
-    the mixed mode (partitioned, partitioned with a warp per line, or block
-    Thomas), then with it the fastest stencil tile shape among `tiles`, each
+    the mixed mode (partitioned, partitioned with a warp per line, partitioned
+    with few lanes per short line, or block Thomas), then with it the fastest stencil tile shape among `tiles`, each
     timed on one scratch solver started from that shape's first case.
     Returns {shape: (SPH_LINES_*, (tj, ti))}."""
     import torch
@@ -62,8 +79,7 @@ def autotune(cases, dt, n_iter, tiles=TILES):
         s = Solver(c.grid, c.par, precision=SPH_PREC_MIXED, stream=torch.cuda.Stream())
         s.set_background(*c.bg)
         init = [torch.from_numpy(np.array(f, dtype=np.float64, copy=True)).cuda() for f in c.init]
-        solvers = (SPH_LINES_PARTITIONED, SPH_LINES_PARTITIONED_WARP, SPH_LINES_THOMAS) \
-            if _partitioned_applies(c.grid) else (SPH_LINES_THOMAS,)
+        solvers = _candidates(c.grid)
         best, best_ms = None, None
         for which in solvers:
             s.set_state(init)

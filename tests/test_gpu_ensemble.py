@@ -104,11 +104,13 @@ def test_autotune_choices_agree():
     cs = _cases()
     choice = ensemble.autotune(cs, 1.0, 2)
     assert set(choice) == {(c.grid.nr, c.grid.nt, c.grid.np) for c in cs}
-    assert all(v[0] in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP)
+    assert all(v[0] in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP,
+                        sph.SPH_LINES_PARTITIONED_NARROW)
                and v[1] in ensemble.TILES for v in choice.values())
-    c = cs[5]   # 64 x 64 x 128: both solvers apply
+    c = cs[5]   # 64 x 64 x 128: every solver applies
     xs = []
-    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP):
+    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED, sph.SPH_LINES_PARTITIONED_WARP,
+                  sph.SPH_LINES_PARTITIONED_NARROW):
         s = _solver(c)
         s.set_line_solver(which)
         for _ in range(2):

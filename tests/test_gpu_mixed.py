@@ -184,6 +184,31 @@ def test_partitioned_sweep_vs_oracle(name, d):
         assert rel_err(x[q], ref[q]) <= 1e-5, (name, d, q, rel_err(x[q], ref[q]))
 
 
+# The narrow layout (4 lanes with chunks of 4 for lines of 16 cells, 8 lanes
+# with chunks of 4, 6 and 8 for 32, 48 and 64): walled and cyclic lines of
+# each length, along every direction, and line counts that leave the last
+# group of a launch partly empty (32 lines a group for 16 and 32 cells, 16
+# for 48 and 64).
+NARROW_CASES = ["shell_16x40x16", "bubble_48x36x16", "sector_16x48x192", "shell_32x20x192", "bubble_64x64x128",
+                "sector_40x256x64", "sector_16x1024x41", "shell_64x36x48", "sector_32x32x33"]
+PART_CASES["shell_64x36x48"] = lambda: _shell((64, 36, 48), pole=False)
+PART_CASES["sector_32x32x33"] = lambda: _sector((32, 32, 33))
+
+
+@pytest.mark.parametrize("name", NARROW_CASES)
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_narrow_sweep_vs_oracle(name, d):
+    g, par, bg, Un, Uk, S, dt = PART_CASES[name]()
+    s = solver_for(g, par, bg, Un, precision=MIXED)
+    s.set_line_solver(sph.SPH_LINES_PARTITIONED_NARROW)
+    s.set_iterate(Uk)
+    rhs = perturbed(g.zeros(), [1.0] * 5, 60 + d, g)
+    x = to_host(s.sweep(d, dt, to_dev(rhs)))
+    ref = oracle.sweep(g, par, Un, Uk, dt, d, rhs, bg=bg)
+    for q in range(5):
+        assert rel_err(x[q], ref[q]) <= 1e-5, (name, d, q, rel_err(x[q], ref[q]))
+
+
 def test_line_solver_option():
     g, par, bg, Un, Uk, S, dt = PART_CASES["shell_64x128x256"]()
     s = solver_for(g, par, bg, Un, precision=MIXED)
@@ -195,12 +220,15 @@ def test_line_solver_option():
         xp = to_host(s.sweep(d, dt, rhs))
         s.set_line_solver(sph.SPH_LINES_PARTITIONED_WARP)
         xw = to_host(s.sweep(d, dt, rhs))
+        s.set_line_solver(sph.SPH_LINES_PARTITIONED_NARROW)
+        xn = to_host(s.sweep(d, dt, rhs))
         s.set_line_solver(sph.SPH_LINES_THOMAS)
         xt = to_host(s.sweep(d, dt, rhs))
         s.set_line_solver(sph.SPH_LINES_PARTITIONED)
         for q in range(5):
             assert rel_err(xp[q], xt[q]) <= 1e-5, (d, q, rel_err(xp[q], xt[q]))
             assert rel_err(xw[q], xt[q]) <= 1e-5, (d, q, rel_err(xw[q], xt[q]))
+            assert rel_err(xn[q], xt[q]) <= 1e-5, (d, q, rel_err(xn[q], xt[q]))
 
 
 @pytest.mark.parametrize("d", [0, 1, 2])
@@ -225,7 +253,7 @@ def test_partitioned_steps_cyclic():
     g, par, bg, Un, Uk, S, dt = PART_CASES["shell_64x128x256"]()
     outs = []
     for prec, which in ((sph.SPH_PREC_FP64, None), (MIXED, sph.SPH_LINES_THOMAS), (MIXED, sph.SPH_LINES_PARTITIONED),
-                        (MIXED, sph.SPH_LINES_PARTITIONED_WARP)):
+                        (MIXED, sph.SPH_LINES_PARTITIONED_WARP), (MIXED, sph.SPH_LINES_PARTITIONED_NARROW)):
         s = solver_for(g, par, bg, Un, precision=prec)
         if which is not None:
             s.set_line_solver(which)

@@ -79,7 +79,7 @@ def test_binding_constants_match_header():
     d = _defines()
     consts = {n: getattr(pkg, n) for n in dir(pkg) if n.startswith("SPH_") and isinstance(getattr(pkg, n), int)}
     assert {"SPH_PREC_FP64", "SPH_PREC_MIXED", "SPH_LINES_THOMAS", "SPH_LINES_PARTITIONED",
-            "SPH_LINES_PARTITIONED_WARP"} <= set(consts)
+            "SPH_LINES_PARTITIONED_WARP", "SPH_LINES_PARTITIONED_NARROW"} <= set(consts)
     for n, v in consts.items():
         assert n in d and d[n] == v, (n, v, d.get(n))
     names = ["avg", "coef", "rhs", "sweep_r", "sweep_theta", "sweep_phi"]
