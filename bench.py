@@ -466,6 +466,9 @@ def run_ensemble(args, rank, world, dist):
             "config": {"workload": "batched ensemble: 64 independent thermal bubbles on the 20 km sector, uneven grids "
                                    "nr in {16,32,48,64}, n_theta and n_phi in {64,128,192,256}, amplitude 0.2-1 K, "
                                    "radius 1-3 km, K=2, dt=1 s, one CUDA graph per two steps",
+                       "launch": ("batched: one kernel per stage and line layout over all instances (instance "
+                                  "descriptor tables in device memory)") if ens.fused else "one graph branch per instance",
+                       "launch_ms_per_step": {("batched" if k else "graph_branches"): v for k, v in ens.mode_ms.items()},
                        "instances": len(specs), "instances_rank0": len(cs), "points": total_pts,
                        "points_rank0": pts, "shapes": shapes,
                        "line_solver": {f"{k[0]}x{k[1]}x{k[2]}": ({0: "thomas", 1: "partitioned", 2: "partitioned_warp", 3: "partitioned_narrow"}[v[0]])
@@ -613,6 +616,8 @@ def main():
             line["ensemble"]["workload"] = e["config"]["workload"]
             line["ensemble"]["line_solver"] = e["config"]["line_solver"]
             line["ensemble"]["tile"] = e["config"]["tile"]
+            line["ensemble"]["launch"] = e["config"]["launch"]
+            line["ensemble"]["launch_ms_per_step"] = e["config"]["launch_ms_per_step"]
         except Exception as ex:   # the headline stands without it
             line["ensemble"] = {"error": str(ex)}
         torch.cuda.empty_cache()

@@ -172,6 +172,20 @@ int sph_adjoint_tape_use(sph_ctx* ctx, int* longest, int* capacity);
 typedef struct sph_batch sph_batch;
 int sph_batch_create(sph_ctx* const* ctxs, int n, void* stream, sph_batch** out);
 int sph_batch_capture(sph_batch* batch, double dt, int n_iter, int steps);
+/* sph_batch_capture_fused: the same graph of `steps` steps built from batched
+ * launches instead of per-context ones -- each stage of an iteration (Ubar,
+ * coefficients, the four right-hand-side kernels, and per sweep one block-line
+ * and one scalar-line launch for each line layout present) is ONE kernel over
+ * every context, reading a per-context descriptor table and a per-block map
+ * (context, tile or line group) from device memory the batch allocates.  The
+ * results are those of per-context steps to FP32 rounding (the same device
+ * code, compiled into other kernels).  Every context must be
+ * in SPH_PREC_MIXED mode with a partitioned line solver that takes all three
+ * directions (line lengths 16, 32, 48, 64, 128, 192, 256; phi also 512,
+ * 1024), without wall data (sph_set_bc) and with per-kernel timing off; else
+ * SPH_ERR_ARG.  The launch counts of a replay are credited to the first
+ * context.  Replay with sph_batch_launch as above. */
+int sph_batch_capture_fused(sph_batch* batch, double dt, int n_iter, int steps);
 int sph_batch_launch(sph_batch* batch, int times);
 int sph_batch_status(sph_batch* batch, int* first_bad);
 void sph_batch_destroy(sph_batch* batch);

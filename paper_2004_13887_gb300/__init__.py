@@ -66,6 +66,7 @@ SIGNATURES = {
     "sph_status": ([_CTX, _DP], C.c_int),
     "sph_batch_create": ([C.POINTER(_CTX), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
     "sph_batch_capture": ([C.c_void_p, C.c_double, C.c_int, C.c_int], C.c_int),
+    "sph_batch_capture_fused": ([C.c_void_p, C.c_double, C.c_int, C.c_int], C.c_int),
     "sph_batch_launch": ([C.c_void_p, C.c_int], C.c_int),
     "sph_batch_status": ([C.c_void_p, C.POINTER(C.c_int)], C.c_int),
     "sph_batch_destroy": ([C.c_void_p], None),
@@ -448,9 +449,14 @@ class Batch:
         self._h = h
         self.steps = 0
 
-    def capture(self, dt: float, n_iter: int, steps: int = 2):
-        _check(load().sph_batch_capture(self._h, float(dt), int(n_iter), int(steps)), "sph_batch_capture")
+    def capture(self, dt: float, n_iter: int, steps: int = 2, fused: bool = False):
+        """Record `steps` steps (even) of every solver into the graph: one branch
+        per solver (fused=False), or batched launches over all solvers, one per
+        stage and line layout (fused=True, sph_batch_capture_fused)."""
+        fn = "sph_batch_capture_fused" if fused else "sph_batch_capture"
+        _check(getattr(load(), fn)(self._h, float(dt), int(n_iter), int(steps)), fn)
         self.steps = steps
+        self.fused = fused
 
     def launch(self, times: int = 1):
         _check(load().sph_batch_launch(self._h, int(times)), "sph_batch_launch")

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libsph.so")
 LIB_CHECKED = os.path.join(HERE, "libsph_checked.so")   # bounds-checked debug build (SPH_CHECKED)
-SOURCES = ["sph.cu", "sph_noalloc.cu", "sph_schur.cu"]
+SOURCES = ["sph.cu", "sph_batch.cu", "sph_noalloc.cu", "sph_schur.cu"]
 HEADERS = ["sph_device.cuh", "sph_kernels.cuh", "sph_host.cuh", "sph_lines.cuh", "sph_adjoint.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -99,10 +99,13 @@ extern "C" long long sph_launch_count(const sph_ctx* ctx) { return ctx ? ctx->la
 
 extern "C" int sph_bounds_report(int* first) {
 #ifdef SPH_CHECKED
-  int h[5] = {0, 0, 0, 0, 0}, z[5] = {0, 0, 0, 0, 0};
+  int h[5] = {0, 0, 0, 0, 0}, z[5] = {0, 0, 0, 0, 0}, hb[5] = {0, 0, 0, 0, 0};
   if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpyFromSymbol(h, g_bounds, sizeof h) != cudaSuccess ||
-      cudaMemcpyToSymbol(g_bounds, z, sizeof z) != cudaSuccess)
+      cudaMemcpyToSymbol(g_bounds, z, sizeof z) != cudaSuccess || bounds_take_batch(hb) != SPH_OK)
     return SPH_ERR_CUDA;
+  if (h[0] == 0)
+    for (int q = 1; q < 5; q++) h[q] = hb[q];
+  h[0] += hb[0];
   if (first)
     for (int q = 0; q < 4; q++) first[q] = h[1 + q];
   return h[0];
@@ -799,27 +802,20 @@ static int lines_prepare(const sph_ctx* c) {
   return e;
 }
 
-// lines of 16, 32, 48 cells: 16 lanes (chunks of 1, 2, 3), or in the narrow
-// layout 4 lanes (chunks of 4) and 8 lanes (chunks of 4, 6); 64: 16 lanes, 32
-// (one warp per line) or 8 (narrow, chunks of 8); 128: 16 lanes unless one
-// warp per line is asked for; 192 and 256: one warp (chunks of 6, 8); phi
-// lines of 512 and 1024: 2 and 4 warps (chunks of 8)
+// the layout lines_pl picks for the context's line solver
 template <int D>
 static int run_lines_d(sph_ctx* c, SweepArgs<float>& S, int n) {
-  const int warp = c->line_solver == SPH_LINES_PARTITIONED_WARP;
-  const int narrow = c->line_solver == SPH_LINES_PARTITIONED_NARROW;
-  if (n == 16) return narrow ? run_lines<D, 4, 4>(c, S) : run_lines<D, 1, 16>(c, S);
-  if (n == 32) return narrow ? run_lines<D, 4, 8>(c, S) : run_lines<D, 2, 16>(c, S);
-  if (n == 48) return narrow ? run_lines<D, 6, 8>(c, S) : run_lines<D, 3, 16>(c, S);
-  if (n == 64 && narrow) return run_lines<D, 8, 8>(c, S);
-  if (n == 192) return run_lines<D, 6, 32>(c, S);
-  if (n == 64) return warp ? run_lines<D, 2, 32>(c, S) : run_lines<D, 4, 16>(c, S);
-  if (n == 128) return warp ? run_lines<D, 4, 32>(c, S) : run_lines<D, 8, 16>(c, S);
+  int P = 0, L = 0;
+  lines_pl(c->line_solver, D, n, &P, &L);
+#define SPH_RUN_PL(p, l) \
+  if (P == p && L == l) return run_lines<D, p, l>(c, S);
+  SPH_LINES_EACH_PL(SPH_RUN_PL)
+#undef SPH_RUN_PL
   if constexpr (D == 2) {
-    if (n == 512) return run_lines<D, 8, 64>(c, S);
-    if (n == 1024) return run_lines<D, 8, 128>(c, S);
+    if (P == 8 && L == 64) return run_lines<D, 8, 64>(c, S);
+    if (P == 8 && L == 128) return run_lines<D, 8, 128>(c, S);
   }
-  return run_lines<D, 8, 32>(c, S);
+  return SPH_ERR_ARG;
 }
 
 template <typename R>
@@ -1249,20 +1245,10 @@ extern "C" int sph_adjoint_tape_use(sph_ctx* c, int* longest, int* capacity) {
 
 // ------------------------------------------------------------ batches
 
-struct sph_batch {
-  int n;
-  sph_ctx** c;
-  cudaStream_t st;
-  cudaEvent_t fork;
-  cudaEvent_t* join;
-  cudaGraph_t graph;
-  cudaGraphExec_t exec;
-  int* cur;                // each context's U^n buffer at capture
-  long long* nlaunch;      // kernels one replay launches per context
-};
 
 extern "C" void sph_batch_destroy(sph_batch* b) {
   if (!b) return;
+  batch_fused_free(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->fork) cudaEventDestroy(b->fork);

@@ -202,7 +202,8 @@ template <typename R> struct MF { R* f[5]; };
 // g_bounds (with the first offending field and (i, j, k)) and the access is
 // redirected to element 0, so that the run goes on and the host reports it.
 #ifdef SPH_CHECKED
-__device__ int g_bounds[5];  // count, field, i, j, k of the first violation
+// (one counter per translation unit: the host merges them)
+static __device__ int g_bounds[5];  // count, field, i, j, k of the first violation
 __device__ __forceinline__ int checked(int f, int i, int j, int k, int ni, int nj, int nk, int idx) {
   if (i < 0 || i >= ni || j < 0 || j >= nj || k < 0 || k >= nk) {
     if (atomicAdd(&g_bounds[0], 1) == 0) { g_bounds[1] = f; g_bounds[2] = i; g_bounds[3] = j; g_bounds[4] = k; }

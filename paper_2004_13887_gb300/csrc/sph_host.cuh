@@ -86,6 +86,34 @@ struct sph_ctx {
   int tape_cap, tape_blocks;
 };
 
+#define SPH_FUSED_STREAMS 8
+
+struct sph_batch {
+  int n;
+  sph_ctx** c;
+  cudaStream_t st;
+  cudaEvent_t fork;
+  cudaEvent_t* join;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  int* cur;                // each context's U^n buffer at capture
+  long long* nlaunch;      // kernels one replay launches per context
+  // batched launches (sph_batch_capture_fused): the descriptor tables and
+  // block maps in one device buffer, side streams for independent launches
+  void* ftab;
+  cudaStream_t fst[SPH_FUSED_STREAMS];
+  cudaEvent_t ffork, fjoin[SPH_FUSED_STREAMS];
+  int fstreams;            // side streams created
+};
+
+// frees what sph_batch_capture_fused allocated (sph_batch.cu)
+void batch_fused_free(sph_batch* b);
+#ifdef SPH_CHECKED
+// the bounds counter of the batched kernels' translation unit into h, then zeroed
+int bounds_take_batch(int* h);
+#endif
+
+
 // Lines of direction d: kind 0 = block lines (a, b) over cell centres, kinds 1/2 =
 // the two transverse velocity components on their interior faces.  Half-open
 // ranges [a_lo, a_hi) x [b_lo, b_hi); (a, b) = (j, k) for d = r, (i, k) for
@@ -145,3 +173,28 @@ static int lines_ok(const sph_ctx* c, int d) {
   return n == 16 || n == 32 || n == 48 || n == 64 || n == 128 || n == 192 || n == 256 ||
          (d == 2 && (n == 512 || n == 1024));
 }
+
+// Partitioned layout of lines of n cells along D for a line solver: P cells per
+// lane, L lanes per line.  Lines of 16, 32, 48 cells: 16 lanes (chunks of 1, 2,
+// 3), or in the narrow layout 4 lanes (chunks of 4) and 8 lanes (chunks of 4,
+// 6); 64: 16 lanes, 32 (one warp per line) or 8 (narrow, chunks of 8); 128: 16
+// lanes unless one warp per line is asked for; 192 and 256: one warp (chunks of
+// 6, 8); phi lines of 512 and 1024: 2 and 4 warps (chunks of 8).
+static inline void lines_pl(int solver, int D, int n, int* P, int* L) {
+  const int warp = solver == SPH_LINES_PARTITIONED_WARP, narrow = solver == SPH_LINES_PARTITIONED_NARROW;
+  int p = 8, l = 32;
+  if (n == 16) { p = narrow ? 4 : 1; l = narrow ? 4 : 16; }
+  else if (n == 32) { p = narrow ? 4 : 2; l = narrow ? 8 : 16; }
+  else if (n == 48) { p = narrow ? 6 : 3; l = narrow ? 8 : 16; }
+  else if (n == 64) { p = narrow ? 8 : warp ? 2 : 4; l = narrow ? 8 : warp ? 32 : 16; }
+  else if (n == 128) { p = warp ? 4 : 8; l = warp ? 32 : 16; }
+  else if (n == 192) { p = 6; l = 32; }
+  else if (D == 2 && n == 512) { p = 8; l = 64; }
+  else if (D == 2 && n == 1024) { p = 8; l = 128; }
+  *P = p;
+  *L = l;
+}
+// every (P, L) of lines_pl in every direction (X(P, L) once each); phi lines of
+// 512 and 1024 add (8, 64) and (8, 128)
+#define SPH_LINES_EACH_PL(X) \
+  X(1, 16) X(4, 4) X(2, 16) X(4, 8) X(3, 16) X(6, 8) X(4, 16) X(2, 32) X(8, 8) X(8, 16) X(4, 32) X(6, 32) X(8, 32)

@@ -150,9 +150,12 @@ __device__ __forceinline__ void coef_at(const Geo<R>& g, const Par& P, const CF<
 // so the default is one phi row; the ensemble's autotuner picks it per grid
 // shape.
 template <typename G>
+__device__ __forceinline__ bool tile_inner_at(const G& g, int i0, int j0, int ti, int tj) {
+  return inner_ij(g, i0, j0) && inner_ij(g, i0 + ti - 1, j0 + tj - 1);
+}
+template <typename G>
 __device__ __forceinline__ bool tile_inner(const G& g) {
-  int i0 = blockIdx.z * blockDim.z, j0 = blockIdx.y * blockDim.y;
-  return inner_ij(g, i0, j0) && inner_ij(g, i0 + (int)blockDim.z - 1, j0 + (int)blockDim.y - 1);
+  return tile_inner_at(g, blockIdx.z * blockDim.z, blockIdx.y * blockDim.y, (int)blockDim.z, (int)blockDim.y);
 }
 // The FP32 stencil kernels are bound by load latency: full occupancy (16
 // blocks of 128 threads, 32 registers) pays for its few register spills
@@ -677,23 +680,56 @@ __device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, SqSum<
   const int NR = cyc ? 4 : 1;
   R Cp[9], dp[12];
   R GiA[9];                     // cyclic: Gam^{-1} A_0
+  // The inputs of cell m + 1 (its centre coefficients, the face values of its
+  // row, its right-hand side) are loaded before cell m is eliminated, so that
+  // their memory latency overlaps the elimination (the forward pass).
+  CPt<R> cqn;
+  FPt<R> fqn;
+  R r0n = R(0), r4n = R(0), run = R(0);
+  auto fetch = [&](int m) {
+    int i, j, k, fi, fj, fk;
+    line_pos(d, a, b, m, i, j, k);
+    const int ic = IC(g, i, j, k);
+    cqn = load_c(S.c, d, ic);
+    fqn = {R(1), R(1), R(0)};
+    run = R(0);
+    if (m < n - 1 || cyc) {
+      next_face(d, n, m, i, j, k, fi, fj, fk);
+      fqn = load_f(g, S.c, S.ub.f[1 + d], d, fi, fj, fk);
+      run = S.rhs.f[1 + d][face_idx(g, d, fi, fj, fk)];
+    }
+    r0n = S.rhs.f[0][ic];
+    r4n = S.rhs.f[4][ic];
+  };
+  if constexpr (!TR) fetch(0);
   for (int m = 0; m < n; m++) {
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
     R A[9], B[9], C[9];
-    if constexpr (TR) transposed_blocks(S, d, n, cyc, a, b, m, A, B, C);
-    else assemble_block(g, S.P, S.c, S.ub, d, n, cyc, m, i, j, k, S.h, A, B, C);
     R rr[12];
-    int ic = IC(g, i, j, k);
-    rr[0] = S.rhs.f[0][ic];
-    rr[NR] = S.rhs.f[4][ic];
-    R ru = R(0);
-    if (m < n - 1 || cyc) {
-      int fi = i, fj = j, fk = k;
-      if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = (m + 1 == n) ? 0 : m + 1;
-      ru = S.rhs.f[1 + d][face_idx(g, d, fi, fj, fk)];
+    if constexpr (TR) {
+      transposed_blocks(S, d, n, cyc, a, b, m, A, B, C);
+      int ic = IC(g, i, j, k);
+      rr[0] = S.rhs.f[0][ic];
+      rr[NR] = S.rhs.f[4][ic];
+      R ru = R(0);
+      if (m < n - 1 || cyc) {
+        int fi = i, fj = j, fk = k;
+        if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = (m + 1 == n) ? 0 : m + 1;
+        ru = S.rhs.f[1 + d][face_idx(g, d, fi, fj, fk)];
+      }
+      rr[2 * NR] = ru;
+    } else {
+      const CPt<R> cq = cqn;
+      const FPt<R> fq = fqn;
+      rr[0] = r0n;
+      rr[NR] = r4n;
+      rr[2 * NR] = run;
+      if (m + 1 < n) fetch(m + 1);
+      int fi, fj, fk;
+      next_face(d, n, m, i, j, k, fi, fj, fk);
+      assemble_pts(g, S.P, cq, fq, d, n, cyc, m, i, j, fi, fj, S.h, A, B, C);
     }
-    rr[2 * NR] = ru;
     if (cyc) {
       // right-hand-side columns 1..3 of U = [Gam; 0; ..; C_{n-1}]
       for (int r = 0; r < 3; r++)
@@ -743,16 +779,27 @@ __device__ void block_line(const SweepArgs<R>& S, int line, int a, int b, SqSum<
       for (int q = 0; q < 3 * NR; q++) s[(9 + q) * nl] = dp[q];
     }
   }
-  // back substitution, all NR columns
+  // back substitution, all NR columns; the factors of cell m - 1 are loaded
+  // before cell m is substituted
   R xs[12];
   for (int q = 0; q < 3 * NR; q++) xs[q] = dp[q];
   R x0[12];
+  R Cn[9], dn[12];
+  if (n >= 2) {
+    const R* s = scr + (n - 2) * W * nl + line;
+    for (int q = 0; q < 9; q++) Cn[q] = s[q * nl];
+    for (int q = 0; q < 3 * NR; q++) dn[q] = s[(9 + q) * nl];
+  }
   for (int m = n - 1; m >= 0; m--) {
     if (m < n - 1) {
-      const R* s = scr + m * W * nl + line;
       R C_[9], d_[12];
-      for (int q = 0; q < 9; q++) C_[q] = s[q * nl];
-      for (int q = 0; q < 3 * NR; q++) d_[q] = s[(9 + q) * nl];
+      for (int q = 0; q < 9; q++) C_[q] = Cn[q];
+      for (int q = 0; q < 3 * NR; q++) d_[q] = dn[q];
+      if (m >= 1) {
+        const R* s = scr + (m - 1) * W * nl + line;
+        for (int q = 0; q < 9; q++) Cn[q] = s[q * nl];
+        for (int q = 0; q < 3 * NR; q++) dn[q] = s[(9 + q) * nl];
+      }
       R xn[12];
       for (int r = 0; r < 3; r++)
         for (int q = 0; q < NR; q++)
@@ -877,10 +924,21 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, SqSum
   const R* rhs = S.rhs.f[1 + cc];
   R cp = R(0), dy = R(0), dz = R(0);
   R a0 = R(0), gam = R(1);
+  // the row inputs and right-hand side of cell m + 1, loaded before cell m is
+  // eliminated (the forward pass)
+  SPt<R> qn;
+  R rn = R(0);
+  auto fetch = [&](int m) {
+    int i, j, k;
+    line_pos(d, a, b, m, i, j, k);
+    qn = load_s<2>(g, S.c, S.ub, cc, d, i, j, k);
+    rn = rhs[face_idx(g, cc, i, j, k)];
+  };
+  if constexpr (!TR) fetch(0);
   for (int m = 0; m < n; m++) {
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    R am, bm, cm;
+    R am, bm, cm, r;
     if constexpr (TR) {
       // row m of the transpose: c_{m-1}, b_m, a_{m+1} (wrapping when cyclic)
       R x0, x1, x2;
@@ -890,8 +948,18 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, SqSum
       if (cyc) { mp = mp < 0 ? n - 1 : mp; mn = mn == n ? 0 : mn; }
       if (mp >= 0) scalar_row(S, cc, d, n, cyc, a, b, mp, x0, x1, am);
       if (mn < n) scalar_row(S, cc, d, n, cyc, a, b, mn, cm, x1, x2);
+      r = rhs[face_idx(g, cc, i, j, k)];
     } else {
-      scalar_row(S, cc, d, n, cyc, a, b, m, am, bm, cm);
+      const SPt<R> q = qn;
+      r = rn;
+      if (m + 1 < n) fetch(m + 1);
+      R w[3];
+      row_sw(g, S.P, q, cc, d, i, j, w);
+      am = S.h * w[0]; bm = R(1) + S.h * w[1]; cm = S.h * w[2];
+      if (!cyc) {
+        if (m == 0) { bm -= am; am = R(0); }
+        if (m == n - 1) { bm -= cm; cm = R(0); }
+      }
     }
     R zr = R(0);
     if (cyc) {
@@ -899,7 +967,6 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, SqSum
       if (m == 0) { a0 = am; gam = -bm; bm -= gam; zr = gam; am = R(0); }
       if (m == n - 1) { bm -= a0 * cm / gam; zr = cm; cm = R(0); }
     }
-    R r = rhs[face_idx(g, cc, i, j, k)];
     R den = bm - am * cp;
     if (den == R(0) || !isfinite(den)) { *bad |= FLAG_SINGULAR; return; }
     R iden = sdiv(R(1), den);
@@ -912,10 +979,14 @@ __device__ void scalar_line(const SweepArgs<R>& S, int line, int a, int b, SqSum
   }
   if (!cyc) {
     R xy = dy;
+    // the factors of cell m - 1 are loaded before cell m is substituted
+    R cn = R(0), yn = R(0);
+    if (n >= 2) { cn = scr[(n - 2) * 3 * nl + line]; yn = scr[(n - 2) * 3 * nl + nl + line]; }
     for (int m = n - 1; m >= 0; m--) {
       if (m < n - 1) {
-        const R* t = scr + m * 3 * nl + line;
-        xy = t[nl] - t[0] * xy;
+        const R c_ = cn, y_ = yn;
+        if (m >= 1) { cn = scr[(m - 1) * 3 * nl + line]; yn = scr[(m - 1) * 3 * nl + nl + line]; }
+        xy = y_ - c_ * xy;
       }
       int i, j, k;
       line_pos(d, a, b, m, i, j, k);

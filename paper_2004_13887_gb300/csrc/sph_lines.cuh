@@ -4,9 +4,9 @@
 // spl1-spl3): 3x3-block tridiagonal systems for (p, T, u_d) and scalar
 // tridiagonal systems for the two transverse velocity components; periodic phi
 // makes the phi lines cyclic.  Here a line of n = L P cells is solved by a
-// segment of L lanes of a warp (L = 32, or 16 with two lines per warp; P = 2,
-// 4, 8): lane l owns the cells [l P, l P + P), and its last cell
-// s_l = l P + P - 1 is a separator.
+// segment of L lanes (L = 32, or 16, 8, 4 with 2, 4, 8 lines per warp, or 64
+// and 128 over several warps; P = 1 to 8): lane l owns the cells
+// [l P, l P + P), and its last cell s_l = l P + P - 1 is a separator.
 //
 //  1. Each lane eliminates its interior cells t = 0..P-2 downwards, treating
 //     the separator before its chunk (s_{l-1}, lane l-1's) as a parameter:
@@ -53,8 +53,8 @@ constexpr unsigned FULL = 0xffffffffu;
 // (none for chunks of one cell, which have no interior)
 __host__ __device__ constexpr int slot_floats(int P) { return (P > 1 ? P - 1 : 0) * NFAC; }
 
-// Shape of a launch: lines of n = L P cells, L lanes per line (16 or 32, or
-// 64 and 128 for lines spanning 2 and 4 warps), P cells per lane; a block
+// Shape of a launch: lines of n = L P cells, L lanes per line (4, 8, 16 or 32,
+// or 64 and 128 for lines spanning 2 and 4 warps), P cells per lane; a block
 // holds NW lines and CB of their cells (NT = CB / P threads, NWW warps; thread
 // w L + l takes lane l of block line w).  In shared memory each staged field
 // is 32 rows of CB/32 values and one word of padding (LS), FS floats in all.
@@ -358,9 +358,10 @@ __device__ __forceinline__ void flush_norms(const SweepArgs<float>& S, const Acc
 // ------------------------------------------------------------------ kernels
 
 // Block lines (p, T, u_D) of direction D, n = L P cells per line, L lanes per
-// line, CB cells per block (at most 128 registers a thread).
+// line, CB cells per block: line group grp (k_lines_blk below, or a batched
+// launch over many problems).
 template <int D, int P, int L, int CB>
-__global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<float> S) {
+__device__ __forceinline__ void lines_blk(const SweepArgs<float>& S, int grp) {
   using SH = Shape<P, L, CB>;
   constexpr int NW = SH::NW, NT = SH::NT, FS = SH::FS;
   extern __shared__ float sm[];
@@ -371,9 +372,9 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
   const float h = S.h;
   SqSum<float> ss;
   int bad = 0;
-  float* slot = S.scr + ((size_t)blockIdx.x * SH::NWW + wid) * (32 * slot_floats(P));
+  float* slot = S.scr + ((size_t)grp * SH::NWW + wid) * (32 * slot_floats(P));
   float* xb = sm + 3 * FS;  // lane exchanges of lines longer than a warp (after the elimination)
-  Group G = group_of(S, 0, blockIdx.x, NW);
+  Group G = group_of(S, 0, grp, NW);
   // 1. stage (n NW = P NT elements: P per thread, all copies in flight).  The
   // block lines past the group's last repeat it, so that every lane of a warp
   // solves a well-posed line; their results are not written back.
@@ -635,6 +636,12 @@ __global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<fl
     }
   }
   flush_norms(S, ss, bad);
+}
+
+// one block per line group (at most 128 registers a thread)
+template <int D, int P, int L, int CB>
+__global__ void __launch_bounds__(CB / P, 512 * P / CB) k_lines_blk(SweepArgs<float> S) {
+  lines_blk<D, P, L, CB>(S, blockIdx.x);
 }
 
 // Scalar lines of the transverse component trans_comp(D, KIND), n = L P, CB

@@ -57,6 +57,100 @@ def test_batch_graph_equals_individual_steps():
     b.close()
 
 
+# every line layout the batched launches take: 16 (narrow 4x4 and 16x1), 32
+# (narrow), 48 (16x3), 64 (narrow, 16x4, one warp), 128 (16x8, one warp), 192,
+# 256, cyclic phi lines (a periodic shell) next to walled ones, and stencil
+# tiles of several shapes in one launch
+FUSED = [((16, 64, 64), sph.SPH_LINES_PARTITIONED_NARROW, (1, 1)),
+         ((32, 64, 128), sph.SPH_LINES_PARTITIONED, (2, 1)),
+         ((16, 128, 64), sph.SPH_LINES_PARTITIONED, (2, 2)),
+         ((48, 64, 64), sph.SPH_LINES_PARTITIONED_WARP, (4, 1)),
+         ((32, 192, 64), sph.SPH_LINES_PARTITIONED_NARROW, (1, 2)),
+         ((64, 64, 128), sph.SPH_LINES_PARTITIONED_WARP, (2, 1)),
+         ((48, 256, 48), sph.SPH_LINES_PARTITIONED_NARROW, (4, 2)),
+         ((64, 128, 256), sph.SPH_LINES_PARTITIONED_NARROW, (1, 1))]
+
+
+def _fused_cases():
+    out = []
+    for q, (n, which, tile) in enumerate(FUSED):
+        out.append((cases.bubble(n, seed=30 + q, dt=1.0, amplitude=0.3 + 0.1 * q, radius=1200.0 + 250.0 * q),
+                    which, tile))
+    # a whole shell (cyclic phi lines of 64, pole faces) among the sectors
+    out.append((cases.shell_low_mach((32, 48, 64), M0=1e-3, dt=1.0), sph.SPH_LINES_PARTITIONED, (1, 1)))
+    return out
+
+
+def _tuned(c, which, tile):
+    s = _solver(c)
+    s.set_line_solver(which)
+    s.set_tile(*tile)
+    return s
+
+
+def test_fused_batch_equals_individual_steps():
+    """The batched launches (one kernel per stage and line layout over every
+    instance, descriptor tables in device memory) give the states of stepping
+    each solver on its own, in far fewer launches.  They run the same device
+    code, compiled into other kernels, where the compiler may contract other
+    FP32 multiply-adds: the increments agree to FP32 rounding (1e-5 of each
+    field's change over the steps), not bit for bit."""
+    cs = _fused_cases()
+    ref, single = [], 0
+    for c, which, tile in cs:
+        s = _tuned(c, which, tile)
+        l0 = s.launches
+        for _ in range(4):
+            s.step(c.dt, 2)
+        single += s.launches - l0
+        ref.append(to_host(s.get_state()))
+        s.close()
+    solvers = [_tuned(c, which, tile) for c, which, tile in cs]
+    b = sph.Batch(solvers)
+    b.capture(1.0, 2, steps=2, fused=True)
+    l0 = sum(s.launches for s in solvers)
+    b.launch(2)
+    b.status()
+    fused = sum(s.launches for s in solvers) - l0
+    worst = 0.0
+    for q, s in enumerate(solvers):
+        got = to_host(s.get_state())
+        c = cs[q][0]
+        for f in range(5):
+            scale = float(np.max(np.abs(ref[q][f] - c.init[f]))) or 1.0
+            err = float(np.max(np.abs(got[f] - ref[q][f]))) / scale
+            worst = max(worst, err)
+            assert err <= 1e-5, ((c.grid.nr, c.grid.nt, c.grid.np), f, err)
+    print(f"batched vs per-instance steps: worst difference {worst:.2e} of a field's change; "
+          f"{fused} launches vs {single}")
+    # per iteration: 6 stencil launches and two per line layout of each
+    # direction (this set has many layouts; the 64-instance ensemble, ~35
+    # launches per iteration against 64 x 12)
+    assert 0 < fused < single / 2, (fused, single)
+    # a replay after the states moved on keeps stepping them (the graph's
+    # tables hold both buffers of every instance)
+    b.launch(1)
+    b.status()
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_fused_batch_refuses_what_it_cannot_batch():
+    cs = _cases()[:2]
+    for prec, which in ((sph.SPH_PREC_FP64, sph.SPH_LINES_PARTITIONED), (MIXED, sph.SPH_LINES_THOMAS)):
+        solvers = [_solver(c, prec) for c in cs]
+        solvers[1].set_line_solver(which)
+        b = sph.Batch(solvers)
+        with pytest.raises(sph.SphError):
+            b.capture(1.0, 2, steps=2, fused=True)
+        with pytest.raises(sph.SphError):
+            b.capture(1.0, 2, steps=3, fused=True)
+        b.close()
+        for s in solvers:
+            s.close()
+
+
 def test_step_async_equals_step():
     c = _cases()[1]
     a, b = _solver(c), _solver(c)

@@ -78,9 +78,11 @@ def test_full_sphere_mixed_error_over_fifty_steps(M0):
         assert errs[k] <= 1e-6, (k, errs)
 
 
-def test_ensemble_instances_vs_oracle():
+@pytest.mark.parametrize("fused", [False, True])
+def test_ensemble_instances_vs_oracle(fused):
     """Three instances of different shapes stepped together by the batched CUDA
-    graph (one branch each), against the oracle stepping each alone."""
+    graph (one branch each, or batched launches over all three), against the
+    oracle stepping each alone."""
     import torch
     specs = [((16, 64, 64), 11), ((32, 64, 128), 12), ((48, 128, 64), 13)]
     cs = [cases.bubble(n, seed=sd, dt=1.0, amplitude=0.5, radius=1800.0) for n, sd in specs]
@@ -90,13 +92,15 @@ def test_ensemble_instances_vs_oracle():
         s.set_background(*c.bg)
         s.set_state(to_dev(c.init))
         solvers.append(s)
+    if fused:
+        solvers[0].set_line_solver(sph.SPH_LINES_PARTITIONED_NARROW)
     b = sph.Batch(solvers)
-    b.capture(1.0, 2, steps=2)
+    b.capture(1.0, 2, steps=2, fused=fused)
     b.launch(2)
     b.status()
     for s, c in zip(solvers, cs):
         errs = field_errors(to_host(s.get_state()), _oracle_steps(c, 4), c.bg, c.par)
-        print("ensemble instance", c.grid.nr, c.grid.nt, c.grid.np, errs)
+        print("ensemble instance", "fused" if fused else "graph", c.grid.nr, c.grid.nt, c.grid.np, errs)
         for k, v in errs.items():
             assert v <= 1e-6, (c.grid, k, v)
     b.close()
