@@ -301,7 +301,7 @@ def run_ours(args, rank, world, dist):
     # FP64 path, timed first (the reference point of the mixed path's error)
     U64 = None
     if args.only in ("both", "fp64"):
-        s64 = sph.Solver(g, c.par, precision=sph.SPH_PREC_FP64)
+        s64 = sph.Solver(g, c.par, precision=sph.SPH_PREC_FP64, stream=torch.cuda.Stream())
         s64.set_background(*c.bg)
         s64.set_state(dev)
         t64, kern64, _, _ = time_path(s64, args, dist, local)
@@ -315,7 +315,7 @@ def run_ours(args, rank, world, dist):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64"}}
 
-    solver = sph.Solver(g, c.par, precision=sph.SPH_PREC_MIXED)
+    solver = sph.Solver(g, c.par, precision=sph.SPH_PREC_MIXED, stream=torch.cuda.Stream())
     solver.set_background(*c.bg)
     solver.set_state(dev)
     stream = solver.stream

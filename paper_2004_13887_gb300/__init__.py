@@ -294,14 +294,33 @@ class Solver:
             arrs.append((_DP * 18)(*ptrs))
         _check(load().sph_set_bc(self._h, arrs[0], arrs[1], int(bool(dev))), "sph_set_bc")
 
+    # The library works on the solver's stream.  Device arrays handed in were
+    # written on torch's current stream, and device arrays handed back are
+    # read there: the two streams are ordered around every such call.
+    def _after_caller(self):
+        import torch
+        cur = torch.cuda.current_stream(self.stream.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _before_caller(self):
+        import torch
+        cur = torch.cuda.current_stream(self.stream.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+
     def set_state(self, fields):
         dev = not isinstance(fields[0], np.ndarray)
         p = _Ptrs(fields, self.shapes, dev)
+        if dev:
+            self._after_caller()
         _check(load().sph_set_state(self._h, p.arr, int(dev)), "sph_set_state")
 
     def set_iterate(self, fields):
         dev = not isinstance(fields[0], np.ndarray)
         p = _Ptrs(fields, self.shapes, dev)
+        if dev:
+            self._after_caller()
         _check(load().sph_set_iterate(self._h, p.arr, int(dev)), "sph_set_iterate")
 
     def empty(self):
@@ -320,12 +339,18 @@ class Solver:
                 if not ok:
                     raise ValueError("out fields must be contiguous, writeable float64 arrays (or CUDA tensors)")
             p = _Ptrs(out, self.shapes, dev)
+            if dev:
+                self._after_caller()
             _check(load().sph_get_state(self._h, p.arr, int(dev)), "sph_get_state")
+            if dev:
+                self._before_caller()
             return out
         if device:
             out = self.empty()
             p = _Ptrs(out, self.shapes, True)
+            self._after_caller()
             _check(load().sph_get_state(self._h, p.arr, 1), "sph_get_state")
+            self._before_caller()
             return out
         out = [np.empty(s) for s in self.shapes]
         p = _Ptrs(out, self.shapes, False)
@@ -340,6 +365,8 @@ class Solver:
             on_dev = int(not isinstance(source[0], np.ndarray))
             src = _Ptrs(source, self.shapes, bool(on_dev))
         res = np.zeros(5) if residual else None
+        if on_dev:
+            self._after_caller()
         _check(load().sph_step(self._h, float(dt), int(n_iter), src.arr if src else None, on_dev,
                                res.ctypes.data_as(_DP) if res is not None else None), "sph_step")
         return res
@@ -347,6 +374,8 @@ class Solver:
     def step_async(self, dt: float, n_iter: int, source=None):
         """Enqueue one step on the solver's stream (device sources only); check with status()."""
         src = _Ptrs(source, self.shapes, True) if source is not None else None
+        if src is not None:
+            self._after_caller()
         _check(load().sph_step_async(self._h, float(dt), int(n_iter), src.arr if src else None, 1), "sph_step_async")
 
     def status(self, residual: bool = False):
@@ -365,8 +394,10 @@ class Solver:
         lo = _Ptrs(lam_out, self.shapes, True)
         li = _Ptrs(lam_in, self.shapes, True)
         src = _Ptrs(source, self.shapes, True) if source is not None else None
+        self._after_caller()
         _check(load().sph_step_adjoint(self._h, float(dt), int(n_iter), src.arr if src else None, lo.arr, li.arr),
                "sph_step_adjoint")
+        self._before_caller()
         return lam_in
 
     def tape_use(self):
@@ -384,14 +415,18 @@ class Solver:
         if source is not None:
             on_dev = int(not isinstance(source[0], np.ndarray))
             src = _Ptrs(source, self.shapes, bool(on_dev))
+        self._after_caller()
         _check(load().sph_rhs(self._h, float(dt), src.arr if src else None, on_dev, po.arr), "sph_rhs")
+        self._before_caller()
         return out
 
     def sweep(self, direction: int, dt: float, rhs_fields):
         out = self.empty()
         pi = _Ptrs(rhs_fields, self.shapes, True)
         po = _Ptrs(out, self.shapes, True)
+        self._after_caller()
         _check(load().sph_sweep(self._h, int(direction), float(dt), pi.arr, po.arr), "sph_sweep")
+        self._before_caller()
         return out
 
     def set_line_solver(self, which: int):
