@@ -37,6 +37,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/sph.h"
 #include "sph_device.cuh"
 
@@ -550,14 +552,27 @@ static int bc_first_iterate(sph_ctx* c) {
 template <typename R> static CF<R> cf_of(R* const* p) { CF<R> r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
 template <typename R> static MF<R> mf_of(R* const* p) { MF<R> r; for (int f = 0; f < 5; f++) r.f[f] = p[f]; return r; }
 
-// bracket a launch: start event before, stop event after (when timing is on)
+// bracket a launch: start event before, stop event after (when timing is on).
+// Each stage's launches are also an NVTX range on the host thread (named
+// "sph <stage>"), so a profiler's timeline and its NVTX filters show the
+// stages; without a tool attached the calls return at once.
+static const char* const kStageName[SPH_NKERNELS] = {"sph avg", "sph coef", "sph rhs", "sph sweep r",
+                                                     "sph sweep theta", "sph sweep phi", "sph other", "sph other"};
+
 static void k_begin(sph_ctx* c, int kind) {
   c->cur_kind = kind;
   c->kcount[kind]++;
+  if (c->nvtx_open) nvtxRangePop();
+  nvtxRangePushA(kStageName[kind]);
+  c->nvtx_open = 1;
   if (c->prof && c->nev < c->evcap) cudaEventRecord(c->ev[2 * c->nev], c->st);
 }
 
 static int launch_ok(sph_ctx* c) {
+  if (c->nvtx_open) {
+    nvtxRangePop();
+    c->nvtx_open = 0;
+  }
   c->launches++;
   if (c->prof && c->nev < c->evcap) {
     cudaEventRecord(c->ev[2 * c->nev + 1], c->st);
@@ -941,6 +956,7 @@ static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> s
   // with wall data, U^{n+1,0} differs from U^n on the normal wall faces: it is
   // formed in the iterate buffer and every iteration reads it from there
   const int first = c->hasbc ? 1 : 0;
+  nvtxRangePushA("sph step");
   if (first) e = bc_first_iterate(c);
   for (int it = 0; it < n_iter && !e; it++) {
     CF<R> ub;
@@ -954,6 +970,11 @@ static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> s
     if (!e && it == n_iter - 1 && cudaMemsetAsync(c->acc, 0, 5 * sizeof(double), c->st) != cudaSuccess) e = SPH_ERR_CUDA;
     if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(b.X1), 1, ukin, mf_of(uk));
   }
+  if (c->nvtx_open) {  // a stage that failed before its launch check
+    nvtxRangePop();
+    c->nvtx_open = 0;
+  }
+  nvtxRangePop();
   return e;
 }
 

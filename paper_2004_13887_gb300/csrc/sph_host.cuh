@@ -49,6 +49,7 @@ struct sph_ctx {
   long unknowns[5];
   // per-kernel timing
   int prof;
+  int nvtx_open;         // a stage's NVTX range is open (k_begin .. launch_ok)
   cudaEvent_t* ev;
   int* evkind;
   int nev, evcap;
