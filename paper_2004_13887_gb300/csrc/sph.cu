@@ -833,6 +833,17 @@ static int run_lines_d(sph_ctx* c, SweepArgs<float>& S, int n) {
   return SPH_ERR_ARG;
 }
 
+// Threads per block of the one-thread-per-line sweeps (k_sweep).  In FP64 mode
+// a block line costs several times a scalar line and the FP64 pipe is the
+// bound: warp-sized blocks spread the block lines evenly over the SMs
+// (measured, 128 x 256 x 256 FP64 step: 64.9 ms at 128 threads a block, 62.6
+// at 64, 60.1 at 32; theta and phi sweeps 13.7 and 15.9 -> 11.7 and 13.2 ms).
+#ifndef SPH_SWEEP64_BLOCK
+#define SPH_SWEEP64_BLOCK 32
+#endif
+template <typename R>
+static constexpr int sweep_block() { return sizeof(R) == sizeof(double) ? SPH_SWEEP64_BLOCK : 128; }
+
 template <typename R>
 static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> rhs, MF<R> x, int update,
                      CF<double> base, MF<double> uk) {
@@ -853,11 +864,12 @@ static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> 
   int mx = S.nl[0];
   if (S.nl[1] > mx) mx = S.nl[1];
   if (S.nl[2] > mx) mx = S.nl[2];
-  dim3 grid((unsigned)((mx + 127) / 128), 3);
+  constexpr int TB = sweep_block<R>();
+  dim3 grid((unsigned)((mx + TB - 1) / TB), 3);
   k_begin(c, SPH_K_SWEEP_R + d);
-  if (d == 0) k_sweep<R, 0><<<grid, 128, 0, c->st>>>(S);
-  else if (d == 1) k_sweep<R, 1><<<grid, 128, 0, c->st>>>(S);
-  else k_sweep<R, 2><<<grid, 128, 0, c->st>>>(S);
+  if (d == 0) k_sweep<R, 0><<<grid, TB, 0, c->st>>>(S);
+  else if (d == 1) k_sweep<R, 1><<<grid, TB, 0, c->st>>>(S);
+  else k_sweep<R, 2><<<grid, TB, 0, c->st>>>(S);
   return launch_ok(c);
 }
 
@@ -1095,10 +1107,11 @@ static int run_sweep_T(sph_ctx* c, int d, double tau, CF<double> ub, CF<double> 
   int mx = S.nl[0];
   if (S.nl[1] > mx) mx = S.nl[1];
   if (S.nl[2] > mx) mx = S.nl[2];
-  dim3 grid((unsigned)((mx + 127) / 128), 3);
-  if (d == 0) k_sweep<double, 0, true><<<grid, 128, 0, c->st>>>(S);
-  else if (d == 1) k_sweep<double, 1, true><<<grid, 128, 0, c->st>>>(S);
-  else k_sweep<double, 2, true><<<grid, 128, 0, c->st>>>(S);
+  constexpr int TB = sweep_block<double>();
+  dim3 grid((unsigned)((mx + TB - 1) / TB), 3);
+  if (d == 0) k_sweep<double, 0, true><<<grid, TB, 0, c->st>>>(S);
+  else if (d == 1) k_sweep<double, 1, true><<<grid, TB, 0, c->st>>>(S);
+  else k_sweep<double, 2, true><<<grid, TB, 0, c->st>>>(S);
   c->launches++;
   return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
 }

@@ -160,7 +160,9 @@ __device__ __forceinline__ bool tile_inner(const G& g) {
 // The FP32 stencil kernels are bound by load latency: full occupancy (16
 // blocks of 128 threads, 32 registers) pays for its few register spills
 // (measured: the right-hand side 17 % faster than at 64 registers).  The FP64
-// instantiations keep their registers.
+// instantiations keep their registers: they are bound by the FP64 pipe, and
+// capping them at 128, 96 or 80 registers (up to 6 blocks an SM) left the
+// FP64 right-hand side at 20.8 ms per step.
 #define STENCIL_MINB(R) (sizeof(R) == 4 ? 16 : 1)
 
 // grid of tiles of tj x ti rows of phi points (128 / (tj ti) each) over an
