@@ -219,8 +219,12 @@ int sph_sweep(sph_ctx* ctx, int dir, double dt, const double* const* rhs, double
  * SPH_LINES_PARTITIONED.  SPH_LINES_THOMAS: block (and scalar) Thomas, one thread per
  * line, with the Woodbury / Sherman-Morrison correction on cyclic lines.  All
  * give the exact solution up to rounding (no pivoting between blocks in any).
- * The FP64 mode always uses block Thomas.  Returns SPH_ERR_ARG for other
- * values. */
+ * The FP64 mode always uses block Thomas: with SPH_LINES_THOMAS one thread per
+ * line; with any other value (the default) two threads per walled line, one
+ * eliminating from each end, the two meeting at the middle cells (a 3x3 solve
+ * there), which halves the dependent chain for the same arithmetic; cyclic
+ * lines keep one thread and the Woodbury correction.  Returns SPH_ERR_ARG for
+ * other values. */
 #define SPH_LINES_THOMAS 0
 #define SPH_LINES_PARTITIONED 1
 #define SPH_LINES_PARTITIONED_WARP 2

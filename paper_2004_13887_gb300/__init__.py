@@ -432,7 +432,9 @@ class Solver:
     def set_line_solver(self, which: int):
         """SPH_LINES_PARTITIONED (default), SPH_LINES_PARTITIONED_WARP (one warp per line),
         SPH_LINES_PARTITIONED_NARROW (4 or 8 lanes for lines of 16 to 64 cells) or
-        SPH_LINES_THOMAS for the mixed-precision sweeps."""
+        SPH_LINES_THOMAS for the mixed-precision sweeps.  In the FP64 mode
+        SPH_LINES_THOMAS takes one thread per line and every other value two
+        threads per walled line (elimination from both ends)."""
         _check(load().sph_set_line_solver(self._h, int(which)), "sph_set_line_solver")
 
     def set_tile(self, tj: int, ti: int):

@@ -865,6 +865,19 @@ static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> 
   if (S.nl[1] > mx) mx = S.nl[1];
   if (S.nl[2] > mx) mx = S.nl[2];
   constexpr int TB = sweep_block<R>();
+  if constexpr (sizeof(R) == sizeof(double)) {
+    if (c->line_solver != SPH_LINES_THOMAS && !(d == 2 && c->d64.g.per)) {
+      // walled lines in the FP64 mode: two threads per line, eliminating from both ends
+      static_assert(TB % 32 == 0, "k_sweep2 takes whole warps");
+      constexpr int LPB = TB / 2;
+      dim3 grid2((unsigned)((mx + LPB - 1) / LPB), 3);
+      k_begin(c, SPH_K_SWEEP_R + d);
+      if (d == 0) k_sweep2<R, 0><<<grid2, TB, 0, c->st>>>(S);
+      else if (d == 1) k_sweep2<R, 1><<<grid2, TB, 0, c->st>>>(S);
+      else k_sweep2<R, 2><<<grid2, TB, 0, c->st>>>(S);
+      return launch_ok(c);
+    }
+  }
   dim3 grid((unsigned)((mx + TB - 1) / TB), 3);
   k_begin(c, SPH_K_SWEEP_R + d);
   if (d == 0) k_sweep<R, 0><<<grid, TB, 0, c->st>>>(S);

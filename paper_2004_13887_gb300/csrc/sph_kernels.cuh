@@ -1042,3 +1042,281 @@ __global__ void __launch_bounds__(128) k_sweep(SweepArgs<R> S) {
     }
   }
 }
+
+// ------------------------------------------------- two-sided line solvers
+// Walled (non-cyclic) lines, forward sweeps: two threads per line, one
+// eliminating downwards from the first cell, the other upwards from the last
+// (block Thomas "burning at both ends"): the same block operations as the
+// one-sided solver above in two dependent chains of half the length, so twice
+// the threads for the same arithmetic.  Lanes 0-15 of a warp take the top side
+// of 16 lines, lanes 16-31 the bottom side of the same lines (partner = lane ^ 16).
+//   top (s = 0), cells 0 .. h-1 (h = ceil(n/2)):  S_m = B_m - A_m E_{m-1},
+//     E_m = S_m^{-1} C_m, g_m = S_m^{-1} (r_m - A_m g_{m-1}),  x_m = g_m - E_m x_{m+1};
+//   bottom (s = 1), cells n-1 .. h, the roles of A and C swapped:
+//     S_m = B_m - C_m E_{m+1}, E_m = S_m^{-1} A_m, g_m = S_m^{-1} (r_m - C_m g_{m+1}),
+//     x_m = g_m - E_m x_{m-1}.
+// At the meeting cells h-1 and h each side solves for its own boundary value,
+// (I - E_o E_p) x_o = g_o - E_o g_p, with the partner's (E_p, g_p) from a
+// shuffle (the same instructions on both sides), then substitutes outwards.
+// Every lane runs the same instructions: a lane past the last line works on
+// the last line and stores nothing; a singular pivot sets the flag and carries
+// NaN on, so that no lane leaves the shuffles early.
+constexpr int SWEEP2_LINES = 16;  // lines per warp
+
+template <typename R>
+__device__ __forceinline__ void inv3_or_nan(const R* S, R* I, int* bad) {
+  if (!inv3(S, I)) {
+    *bad |= FLAG_SINGULAR;
+#pragma unroll
+    for (int q = 0; q < 9; q++) I[q] = R(NAN);
+  }
+}
+
+template <typename R, int D>
+__device__ void block_line2(const SweepArgs<R>& S, int line, bool valid, int a, int b, int side, SqSum<R>& ss,
+                            int* bad) {
+  const Geo<R>& g = S.g;
+  constexpr int d = D;
+  const int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
+  const int nl = S.nl[0];
+  R* scr = S.scr + S.scr_off[0];
+  constexpr int W = 12;
+  const int h = (n + 1) / 2;
+  const int cnt = side ? n - h : h;  // cells of this side (the bottom side of a one-cell line has none)
+  auto cell = [&](int s) { return side ? n - 1 - s : s; };
+  CPt<R> cqn;
+  FPt<R> fqn;
+  R r0n = R(0), r4n = R(0), run = R(0);
+  auto fetch = [&](int m) {
+    int i, j, k, fi, fj, fk;
+    line_pos(d, a, b, m, i, j, k);
+    const int ic = IC(g, i, j, k);
+    cqn = load_c(S.c, d, ic);
+    fqn = {R(1), R(1), R(0)};
+    run = R(0);
+    if (m < n - 1) {
+      next_face(d, n, m, i, j, k, fi, fj, fk);
+      fqn = load_f(g, S.c, S.ub.f[1 + d], d, fi, fj, fk);
+      run = S.rhs.f[1 + d][face_idx(g, d, fi, fj, fk)];
+    }
+    r0n = S.rhs.f[0][ic];
+    r4n = S.rhs.f[4][ic];
+  };
+  R E[9], gv[3];
+#pragma unroll
+  for (int q = 0; q < 9; q++) E[q] = R(0);
+  gv[0] = gv[1] = gv[2] = R(0);
+  if (cnt > 0) fetch(cell(0));
+  for (int s = 0; s < cnt; s++) {
+    const int m = cell(s);
+    int i, j, k;
+    line_pos(d, a, b, m, i, j, k);
+    R A[9], B[9], C[9];
+    const CPt<R> cq = cqn;
+    const FPt<R> fq = fqn;
+    R rr[3] = {r0n, r4n, run};
+    if (s + 1 < cnt) fetch(cell(s + 1));
+    int fi, fj, fk;
+    next_face(d, n, m, i, j, k, fi, fj, fk);
+    assemble_pts(g, S.P, cq, fq, d, n, 0, m, i, j, fi, fj, S.h, A, B, C);
+    // L couples to the cell already eliminated, U to the next one
+    R L[9], U[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) { L[q] = side ? C[q] : A[q]; U[q] = side ? A[q] : C[q]; }
+    R Sm[9], y[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+#pragma unroll
+      for (int q = 0; q < 3; q++)
+        Sm[r * 3 + q] = B[r * 3 + q] - (L[r * 3] * E[q] + L[r * 3 + 1] * E[3 + q] + L[r * 3 + 2] * E[6 + q]);
+      y[r] = rr[r] - (L[r * 3] * gv[0] + L[r * 3 + 1] * gv[1] + L[r * 3 + 2] * gv[2]);
+    }
+    R Si[9];
+    inv3_or_nan(Sm, Si, bad);
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+#pragma unroll
+      for (int q = 0; q < 3; q++) E[r * 3 + q] = Si[r * 3] * U[q] + Si[r * 3 + 1] * U[3 + q] + Si[r * 3 + 2] * U[6 + q];
+      gv[r] = Si[r * 3] * y[0] + Si[r * 3 + 1] * y[1] + Si[r * 3 + 2] * y[2];
+    }
+    if (s + 1 < cnt && valid) {
+      R* sp = scr + m * W * nl + line;
+#pragma unroll
+      for (int q = 0; q < 9; q++) sp[q * nl] = E[q];
+#pragma unroll
+      for (int q = 0; q < 3; q++) sp[(9 + q) * nl] = gv[q];
+    }
+  }
+  // the meeting cells: the partner's last factors (zero for the empty bottom
+  // side of a one-cell line, which leaves x = g on the top side)
+  R Ep[9], gp[3];
+#pragma unroll
+  for (int q = 0; q < 9; q++) Ep[q] = __shfl_xor_sync(0xffffffffu, E[q], 16);
+#pragma unroll
+  for (int q = 0; q < 3; q++) gp[q] = __shfl_xor_sync(0xffffffffu, gv[q], 16);
+  R Mm[9], rhs[3], Mi[9], xs[3];
+#pragma unroll
+  for (int r = 0; r < 3; r++) {
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+      Mm[r * 3 + q] = (r == q ? R(1) : R(0)) - (E[r * 3] * Ep[q] + E[r * 3 + 1] * Ep[3 + q] + E[r * 3 + 2] * Ep[6 + q]);
+    rhs[r] = gv[r] - (E[r * 3] * gp[0] + E[r * 3 + 1] * gp[1] + E[r * 3 + 2] * gp[2]);
+  }
+  inv3_or_nan(Mm, Mi, bad);
+#pragma unroll
+  for (int r = 0; r < 3; r++) xs[r] = Mi[r * 3] * rhs[0] + Mi[r * 3 + 1] * rhs[1] + Mi[r * 3 + 2] * rhs[2];
+  // substitution outwards from the meeting cell; the factors of the next cell
+  // out are loaded before the current one is stored
+  R En[9], gn[3];
+  if (cnt >= 2) {
+    const R* sp = scr + cell(cnt - 2) * W * nl + line;
+#pragma unroll
+    for (int q = 0; q < 9; q++) En[q] = sp[q * nl];
+#pragma unroll
+    for (int q = 0; q < 3; q++) gn[q] = sp[(9 + q) * nl];
+  }
+  for (int s = cnt - 1; s >= 0; s--) {
+    const int m = cell(s);
+    if (s < cnt - 1) {
+      R E_[9], g_[3];
+#pragma unroll
+      for (int q = 0; q < 9; q++) E_[q] = En[q];
+#pragma unroll
+      for (int q = 0; q < 3; q++) g_[q] = gn[q];
+      if (s >= 1) {
+        const R* sp = scr + cell(s - 1) * W * nl + line;
+#pragma unroll
+        for (int q = 0; q < 9; q++) En[q] = sp[q * nl];
+#pragma unroll
+        for (int q = 0; q < 3; q++) gn[q] = sp[(9 + q) * nl];
+      }
+      R xn[3];
+#pragma unroll
+      for (int r = 0; r < 3; r++) xn[r] = g_[r] - (E_[r * 3] * xs[0] + E_[r * 3 + 1] * xs[1] + E_[r * 3 + 2] * xs[2]);
+#pragma unroll
+      for (int q = 0; q < 3; q++) xs[q] = xn[q];
+    }
+    if (valid) {
+      int i, j, k;
+      line_pos(d, a, b, m, i, j, k);
+      int ic = IC(g, i, j, k);
+      put(S, 0, ic, xs[0], ss, bad);
+      put(S, 4, ic, xs[1], ss, bad);
+      int fi = i, fj = j, fk = k;
+      if (m < n - 1) {
+        if (d == 0) fi = m + 1; else if (d == 1) fj = m + 1; else fk = m + 1;
+        put(S, 1 + d, face_idx(g, d, fi, fj, fk), xs[2], ss, bad);
+      } else {
+        if (d == 0) fi = n; else if (d == 1) fj = n; else fk = n;
+        put_wall(S, 1 + d, face_idx(g, d, fi, fj, fk));
+        int gi = i, gj = j, gk = k;
+        if (d == 0) gi = 0; else if (d == 1) gj = 0; else gk = 0;
+        put_wall(S, 1 + d, face_idx(g, d, gi, gj, gk));
+      }
+    }
+  }
+}
+
+// The scalar (transverse-component) lines the same way: Thomas from both ends,
+// (1 - e_o e_p) x_o = g_o - e_o g_p at the meeting cells.
+template <typename R, int D, int KIND>
+__device__ void scalar_line2(const SweepArgs<R>& S, int line, bool valid, int a, int b, int side, SqSum<R>& ss,
+                             int* bad) {
+  const Geo<R>& g = S.g;
+  constexpr int d = D, kind = KIND;
+  const int cc = trans_comp(d, kind);
+  const int n = d == 0 ? g.nr : d == 1 ? g.nt : g.np;
+  const int nl = S.nl[kind];
+  R* scr = S.scr + S.scr_off[kind];
+  const R* rhs = S.rhs.f[1 + cc];
+  const int h = (n + 1) / 2;
+  const int cnt = side ? n - h : h;
+  auto cell = [&](int s) { return side ? n - 1 - s : s; };
+  SPt<R> qn;
+  R rn = R(0);
+  auto fetch = [&](int m) {
+    int i, j, k;
+    line_pos(d, a, b, m, i, j, k);
+    qn = load_s<2>(g, S.c, S.ub, cc, d, i, j, k);
+    rn = rhs[face_idx(g, cc, i, j, k)];
+  };
+  R e = R(0), gy = R(0);
+  if (cnt > 0) fetch(cell(0));
+  for (int s = 0; s < cnt; s++) {
+    const int m = cell(s);
+    int i, j, k;
+    line_pos(d, a, b, m, i, j, k);
+    const SPt<R> q = qn;
+    const R r = rn;
+    if (s + 1 < cnt) fetch(cell(s + 1));
+    R w[3];
+    row_sw(g, S.P, q, cc, d, i, j, w);
+    R am = S.h * w[0], bm = R(1) + S.h * w[1], cm = S.h * w[2];
+    if (m == 0) { bm -= am; am = R(0); }
+    if (m == n - 1) { bm -= cm; cm = R(0); }
+    const R lo = side ? cm : am, up = side ? am : cm;
+    R den = bm - lo * e;
+    if (den == R(0) || !isfinite(den)) *bad |= FLAG_SINGULAR;
+    R iden = sdiv(R(1), den);
+    e = up * iden;
+    gy = (r - lo * gy) * iden;
+    if (s + 1 < cnt && valid) {
+      R* sp = scr + m * 3 * nl + line;
+      sp[0] = e;
+      sp[nl] = gy;
+    }
+  }
+  const R ep = __shfl_xor_sync(0xffffffffu, e, 16), gp = __shfl_xor_sync(0xffffffffu, gy, 16);
+  R x = sdiv(gy - e * gp, R(1) - e * ep);
+  R en = R(0), gn = R(0);
+  if (cnt >= 2) {
+    const int mm = cell(cnt - 2);
+    en = scr[mm * 3 * nl + line];
+    gn = scr[mm * 3 * nl + nl + line];
+  }
+  for (int s = cnt - 1; s >= 0; s--) {
+    const int m = cell(s);
+    if (s < cnt - 1) {
+      const R e_ = en, g_ = gn;
+      if (s >= 1) {
+        const int mm = cell(s - 1);
+        en = scr[mm * 3 * nl + line];
+        gn = scr[mm * 3 * nl + nl + line];
+      }
+      x = g_ - e_ * x;
+    }
+    if (valid) {
+      int i, j, k;
+      line_pos(d, a, b, m, i, j, k);
+      scalar_put(S, cc, i, j, k, x, ss, bad);
+    }
+  }
+}
+
+// one warp per 16 lines of one kind (blockIdx.y): lanes l and l + 16 share a line
+template <typename R, int D>
+__global__ void __launch_bounds__(128) k_sweep2(SweepArgs<R> S) {
+  const int kind = blockIdx.y;
+  const int nl = S.nl[kind];
+  const int lane = threadIdx.x & 31;
+  const int base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) / 2;  // first line of the warp
+  if (base >= nl) return;  // the whole warp: no line of this kind left
+  const int side = lane >> 4;
+  const int l0 = base + (lane & (SWEEP2_LINES - 1));
+  const bool valid = l0 < nl;
+  const int line = valid ? l0 : nl - 1;
+  SqSum<R> ss;
+  int bad = 0;
+  int a = (int)(line / S.nb[kind]) + S.a0[kind];
+  int b = (int)(line % S.nb[kind]) + S.b0[kind];
+  if (kind == 0) block_line2<R, D>(S, line, valid, a, b, side, ss, &bad);
+  else if (kind == 1) scalar_line2<R, D, 1>(S, line, valid, a, b, side, ss, &bad);
+  else scalar_line2<R, D, 2>(S, line, valid, a, b, side, ss, &bad);
+  if (bad) atomicOr(S.flag, bad);
+  if (S.update) {
+    for (int f = 0; f < 5; f++) {
+      double v = ss.warp_total(f);
+      if (lane == 0 && v != 0.0) atomicAdd(S.acc + f, v);
+    }
+  }
+}

@@ -117,6 +117,28 @@ def test_sweep_parity(name, d):
         assert rel_err(x[q], ref[q]) <= 1e-12, (name, d, q, rel_err(x[q], ref[q]))
 
 
+@pytest.mark.parametrize("name", ["sector", "bubble", "tiny", "ragged"])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_sweep_parity_fp64_both_line_forms(name, d):
+    """FP64 walled lines: one thread per line (SPH_LINES_THOMAS) and two threads
+    per line eliminating from both ends (the default) both within 1e-12 of the
+    oracle's block Thomas, on even and odd line lengths down to two cells."""
+    g, par, bg, Un, Uk, S, dt = CASES[name]()
+    rhs = perturbed(g.zeros(), [1.0] * 5, 30 + d, g)
+    ref = oracle.sweep(g, par, Un, Uk, dt, d, rhs, bg=bg)
+    out = {}
+    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED):
+        s = solver_for(g, par, bg, Un)
+        s.set_line_solver(which)
+        s.set_iterate(Uk)
+        out[which] = to_host(s.sweep(d, dt, to_dev(rhs)))
+        s.close()
+        for q in range(5):
+            assert rel_err(out[which][q], ref[q]) <= 1e-12, (name, d, which, q, rel_err(out[which][q], ref[q]))
+    for q in range(5):
+        assert rel_err(out[sph.SPH_LINES_PARTITIONED][q], out[sph.SPH_LINES_THOMAS][q]) <= 1e-12, (name, d, q)
+
+
 def _steps(g, par, bg, U0, dt, K, nsteps, source=None):
     s = solver_for(g, par, bg, U0)
     Uo = U0
