@@ -72,7 +72,9 @@ size_t sph_field_size(const sph_grid* grid, int f);
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL =
  * legacy default stream).  The context owns all device buffers (state U^n,
- * iterate U^{n+1,k}, coefficients, right-hand sides, line-solve scratch).
+ * iterate U^{n+1,k}, coefficients, right-hand sides, line-solve scratch; in
+ * SPH_PREC_FP64 also the line rows of D_r, D_theta, D_phi that each step's
+ * right-hand side stores for its sweeps, about 45 doubles per cell).
  * Errors: SPH_ERR_ARG (nr, nth, nph < 2; r1 <= 0; empty ranges; periodic with
  * nph < 3; a grid too large for the kernels' 32-bit indexing: every field and
  * the line-solve scratch, 18 values per cell (27 with periodic phi), must stay

@@ -141,7 +141,7 @@ static void free_all(sph_ctx* c) {
   if (c->efork) cudaEventDestroy(c->efork);
   bufs_free(c->d64);
   bufs_free(c->d32);
-  cudaFree(c->bg); cudaFree(c->acc); cudaFree(c->flag);
+  cudaFree(c->bg); cudaFree(c->acc); cudaFree(c->flag); cudaFree(c->rows64);
   cudaFree(c->wmean64); cudaFree(c->wmean32); cudaFree(c->wnext);
   cudaFree(c->wzero64); cudaFree(c->wzero32);
   cudaFree(c->adjS); cudaFree(c->adjW); cudaFree(c->adjC);
@@ -361,6 +361,23 @@ extern "C" int sph_create(const sph_grid* gr, const sph_params* pa, void* stream
                         !cuda_ok(cudaMalloc((void**)&c->acc, 8 * sizeof(double))) ||
                         !cuda_ok(cudaMalloc((void**)&c->flag, sizeof(int)))))
     err = SPH_ERR_NOMEM;
+  if (err == SPH_OK && !mixed) {
+    // the line rows of the FP64 mode: 12 planes over the centres per direction,
+    // 5 + 6 over the faces of each kind
+    size_t nrows = 36 * (size_t)c->N + 11 * (c->nf[1] + c->nf[2] + c->nf[3]);
+    if (!cuda_ok(cudaMalloc((void**)&c->rows64, nrows * sizeof(double)))) {
+      err = SPH_ERR_NOMEM;
+    } else {
+      double* p = c->rows64;
+      c->rows.nc = c->N;
+      for (int d = 0; d < 3; d++) { c->rows.c[d] = p; p += 12 * (size_t)c->N; }
+      for (int d = 0; d < 3; d++) {
+        c->rows.nf[d] = (long)c->nf[1 + d];
+        c->rows.f[d] = p; p += 5 * c->nf[1 + d];
+        c->rows.s[d] = p; p += 6 * c->nf[1 + d];
+      }
+    }
+  }
   if (err != SPH_OK) { cudaGetLastError(); free_all(c); free(c); return err; }
   if (!cuda_ok(cudaMemset(c->bg, 0, 2 * (size_t)(nr + 2) * sizeof(double))) || !cuda_ok(cudaMemset(c->flag, 0, sizeof(int))))
     err = SPH_ERR_CUDA;
@@ -678,28 +695,31 @@ static int run_rhs(sph_ctx* c, Bufs<R>& b, CF<R> ub, CF<double> uk, int hasD, do
   CF<R> Dv = cf_of(b.Db);  // U^k - U^n from the averaging stage (zero, and not read, when hasD = 0)
   CF<R> ul = sizeof(R) == sizeof(float) ? cf_of(b.UbLo) : ub;  // velocity remainders of Ubar (FP32 mode)
   R tr = (R)tau;
+  // FP64 mode: the kernels also store the line rows the sweeps read
+  Rows64 rows = c->rows;
+  if (sizeof(R) != sizeof(double)) memset(&rows, 0, sizeof rows);
   k_begin(c, SPH_K_RHS);
   if (fork_aux(c, 3)) return SPH_ERR_CUDA;
   const Geo<double>& gg = c->d64.g;
   int nr = gg.nr, nt = gg.nt, np = gg.np, npf = gg.npf;
   if (b.g.hasw) {
     k_rhs_c<R, true><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv,
-                                                                      hasD, src, has_src, tr, Rout);
+                                                                      hasD, src, has_src, tr, Rout, rows);
     k_rhs_u<R, 0, true><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->aux[0]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
-                                                                                 has_src, tr, Rout);
+                                                                                 has_src, tr, Rout, rows);
     k_rhs_u<R, 1, true><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->aux[1]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
-                                                                                 has_src, tr, Rout);
+                                                                                 has_src, tr, Rout, rows);
     k_rhs_u<R, 2, true><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->aux[2]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
-                                                                              has_src, tr, Rout);
+                                                                              has_src, tr, Rout, rows);
   } else {
     k_rhs_c<R, false><<<tile_grid(np, nt, nr), TILE_BLOCK, 0, c->st>>>(b.g, c->d64.g, c->P, b.c, ub, ul, un, uk, Dv,
-                                                                       hasD, src, has_src, tr, Rout);
+                                                                       hasD, src, has_src, tr, Rout, rows);
     k_rhs_u<R, 0, false><<<tile_grid(np, nt, nr + 1), TILE_BLOCK, 0, c->aux[0]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
-                                                                                  has_src, tr, Rout);
+                                                                                  has_src, tr, Rout, rows);
     k_rhs_u<R, 1, false><<<tile_grid(np, nt + 1, nr), TILE_BLOCK, 0, c->aux[1]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
-                                                                                  has_src, tr, Rout);
+                                                                                  has_src, tr, Rout, rows);
     k_rhs_u<R, 2, false><<<tile_grid(npf, nt, nr), TILE_BLOCK, 0, c->aux[2]>>>(b.g, c->P, b.c, ub, Dv, hasD, src,
-                                                                               has_src, tr, Rout);
+                                                                               has_src, tr, Rout, rows);
   }
   if (join_aux(c, 3)) return SPH_ERR_CUDA;
   c->launches += 3;  // launch_ok counts the fourth
@@ -846,12 +866,13 @@ static constexpr int sweep_block() { return sizeof(R) == sizeof(double) ? SPH_SW
 
 template <typename R>
 static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> rhs, MF<R> x, int update,
-                     CF<double> base, MF<double> uk) {
+                     CF<double> base, MF<double> uk, int rows_ready = 0) {
   SweepArgs<R> S;
   memset(&S, 0, sizeof S);
   S.g = b.g; S.P = c->P; S.c = b.c; S.ub = ub; S.d = d; S.h = (R)(0.5 * tau);
   S.rhs = rhs; S.x = x; S.update = update; S.base = base; S.uk = uk;
   S.scr = b.scr; S.acc = c->acc; S.flag = c->flag;
+  S.rows = c->rows;
   line_layout(c->d64.g, d, S);
   if (sizeof(R) == sizeof(float) && c->line_solver != SPH_LINES_THOMAS && lines_ok(c, d)) {
     SweepArgs<float>& Sf = *reinterpret_cast<SweepArgs<float>*>(&S);
@@ -872,9 +893,17 @@ static int run_sweep(sph_ctx* c, Bufs<R>& b, int d, double tau, CF<R> ub, CF<R> 
       constexpr int LPB = TB / 2;
       dim3 grid2((unsigned)((mx + LPB - 1) / LPB), 3);
       k_begin(c, SPH_K_SWEEP_R + d);
-      if (d == 0) k_sweep2<R, 0><<<grid2, TB, 0, c->st>>>(S);
-      else if (d == 1) k_sweep2<R, 1><<<grid2, TB, 0, c->st>>>(S);
-      else k_sweep2<R, 2><<<grid2, TB, 0, c->st>>>(S);
+      // rows_ready: the right-hand side of this iteration has just stored the
+      // line rows (steps); a sweep on its own (sph_sweep) forms them
+      if (rows_ready && c->rows64) {
+        if (d == 0) k_sweep2<R, 0, true><<<grid2, TB, 0, c->st>>>(S);
+        else if (d == 1) k_sweep2<R, 1, true><<<grid2, TB, 0, c->st>>>(S);
+        else k_sweep2<R, 2, true><<<grid2, TB, 0, c->st>>>(S);
+      } else {
+        if (d == 0) k_sweep2<R, 0, false><<<grid2, TB, 0, c->st>>>(S);
+        else if (d == 1) k_sweep2<R, 1, false><<<grid2, TB, 0, c->st>>>(S);
+        else k_sweep2<R, 2, false><<<grid2, TB, 0, c->st>>>(S);
+      }
       return launch_ok(c);
     }
   }
@@ -990,10 +1019,10 @@ static int step_impl(sph_ctx* c, Bufs<R>& b, double dt, int n_iter, CF<double> s
     if (e) break;
     CF<double> ukin = cf_of(iter ? uk : un);
     e = run_rhs(c, b, ub, ukin, iter, dt, src, has, mf_of(b.Rb));
-    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, ukin, mf_of(uk));
-    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, ukin, mf_of(uk));
+    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, ukin, mf_of(uk), 1);
+    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, ukin, mf_of(uk), 1);
     if (!e && it == n_iter - 1 && cudaMemsetAsync(c->acc, 0, 5 * sizeof(double), c->st) != cudaSuccess) e = SPH_ERR_CUDA;
-    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(b.X1), 1, ukin, mf_of(uk));
+    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(b.X1), 1, ukin, mf_of(uk), 1);
   }
   if (c->nvtx_open) {  // a stage that failed before its launch check
     nvtxRangePop();
@@ -1219,9 +1248,9 @@ extern "C" int sph_step_adjoint(sph_ctx* c, double dt, int n_iter, const double*
     CF<double> ub;
     e = prepare(c, b, iter, &ub, Sk);
     if (!e) e = run_rhs(c, b, ub, cf_of(iter ? Sk : un), iter, dt, src, has, mf_of(b.Rb));
-    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, cf_of(Sk), mf_of(Sn));
-    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, cf_of(Sk), mf_of(Sn));
-    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(Sn), 1, cf_of(Sk), mf_of(Sn));
+    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(b.X1), 0, cf_of(Sk), mf_of(Sn), 1);
+    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(b.X1), mf_of(b.Rb), 0, cf_of(Sk), mf_of(Sn), 1);
+    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(b.Rb), mf_of(Sn), 1, cf_of(Sk), mf_of(Sn), 1);
   }
   // reverse
   if (!e && cudaMemsetAsync(LN[0], 0, FB, c->st) != cudaSuccess) e = SPH_ERR_CUDA;
@@ -1236,9 +1265,9 @@ extern "C" int sph_step_adjoint(sph_ctx* c, double dt, int n_iter, const double*
     // the iteration's Ubar, coefficients and sweep solutions
     e = prepare(c, b, iter, &ub, Sk);
     if (!e) e = run_rhs(c, b, ub, cf_of(iter ? Sk : un), iter, dt, src, has, mf_of(b.Rb));
-    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(XS[0]), 0, cf_of(Sk), mf_of(Sk));
-    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(XS[0]), mf_of(XS[1]), 0, cf_of(Sk), mf_of(Sk));
-    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(XS[1]), mf_of(XS[2]), 0, cf_of(Sk), mf_of(Sk));
+    if (!e) e = run_sweep(c, b, 0, dt, ub, cf_of(b.Rb), mf_of(XS[0]), 0, cf_of(Sk), mf_of(Sk), 1);
+    if (!e) e = run_sweep(c, b, 1, dt, ub, cf_of(XS[0]), mf_of(XS[1]), 0, cf_of(Sk), mf_of(Sk), 1);
+    if (!e) e = run_sweep(c, b, 2, dt, ub, cf_of(XS[1]), mf_of(XS[2]), 0, cf_of(Sk), mf_of(Sk), 1);
     // transposed solves, phi first
     if (!e) e = run_sweep_T(c, 2, dt, ub, cf_of(LB), mf_of(MU[2]));
     if (!e) e = run_sweep_T(c, 1, dt, ub, cf_of(MU[2]), mf_of(MU[1]));

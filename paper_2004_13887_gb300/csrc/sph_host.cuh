@@ -45,6 +45,8 @@ struct sph_ctx {
   size_t nmet;
   Bufs<double> d64;      // FP64 metric/background tables always; bulk buffers in FP64 mode
   Bufs<float> d32;       // bulk buffers in mixed mode
+  double* rows64;        // FP64 mode: the line rows the right-hand side stores for the sweeps
+  Rows64 rows;           // pointers into rows64 (all null in mixed mode)
   long long launches;
   long unknowns[5];
   // per-kernel timing

@@ -249,14 +249,69 @@ __device__ __forceinline__ R div_ubar_of(const Geo<R>& g, const CF<R>& ub, int i
   return dr_ + dt_ + dp_;
 }
 
+// Line rows of the FP64 mode.  The right-hand side evaluates, at every unknown,
+// the rows of D_r, D_theta and D_phi at Ubar -- the same rows each sweep's line
+// matrix I + tau/2 D_d is assembled from.  In the FP64 mode the arithmetic, not
+// memory, bounds the step, so the right-hand side stores the rows it has formed
+// and the sweeps read them instead of forming them again (45 doubles a cell).
+//   c[d]: 12 planes over the centres, the p- and T-rows of D_d: p-row wp0, wp2,
+//         wT0, wT1, wT2, v0, v1 (wp1 is zero: advection has no diagonal); T-row
+//         wT0, wT1, wT2, v0, v1; v_q = a gd_q + wv_q (the u_d couplings);
+//   f[d]: 5 planes over the d-faces, the normal-velocity row of D_d (wp0, wp1,
+//         wu0, wu1, wu2);
+//   s[c]: 6 planes over the c-faces, the rows of velocity component c along its
+//         two transverse directions in increasing order (3 weights each).
+// NoRows (every other caller) stores nothing.
+struct NoRows { static constexpr bool on = false; };
+struct Rows64 {
+  static constexpr bool on = true;
+  double* c[3];
+  double* f[3];
+  double* s[3];
+  long nc, nf[3];  // centres; faces of each kind
+};
+// slot of direction d among the transverse directions of component cc
+__host__ __device__ constexpr int trans_slot(int cc, int d) { return d < cc ? d : d - 1; }
+
+template <typename RowsT, typename R>
+__device__ __forceinline__ void rows_put_c(const RowsT& o, int d, int isT, int t, const RowC<R>& w) {
+  if constexpr (RowsT::on && std::is_same<R, double>::value) {
+    double* p = o.c[d] + t;
+    const long n = o.nc;
+    if (!isT) {
+      p[0] = w.wp[0]; p[n] = w.wp[2]; p[2 * n] = w.wT[0]; p[3 * n] = w.wT[1]; p[4 * n] = w.wT[2];
+      p[5 * n] = w.a * w.gd[0] + w.wv[0]; p[6 * n] = w.a * w.gd[1] + w.wv[1];
+    } else {
+      p[7 * n] = w.wT[0]; p[8 * n] = w.wT[1]; p[9 * n] = w.wT[2];
+      p[10 * n] = w.a * w.gd[0] + w.wv[0]; p[11 * n] = w.a * w.gd[1] + w.wv[1];
+    }
+  }
+}
+template <typename RowsT, typename R>
+__device__ __forceinline__ void rows_put_f(const RowsT& o, int d, int t, const R* wp, const R* wu) {
+  if constexpr (RowsT::on && std::is_same<R, double>::value) {
+    double* p = o.f[d] + t;
+    const long n = o.nf[d];
+    p[0] = wp[0]; p[n] = wp[1]; p[2 * n] = wu[0]; p[3 * n] = wu[1]; p[4 * n] = wu[2];
+  }
+}
+template <typename RowsT, typename R>
+__device__ __forceinline__ void rows_put_s(const RowsT& o, int cc, int d, int t, const R* w) {
+  if constexpr (RowsT::on && std::is_same<R, double>::value) {
+    const long n = o.nf[cc];
+    double* p = o.s[cc] + 3 * trans_slot(cc, d) * n + t;
+    p[0] = w[0]; p[n] = w[1]; p[2 * n] = w[2];
+  }
+}
+
 // R = -(U^k - U^n) - tau (N(Ubar) + G - S) for the p- and T-rows: one thread per
 // centre; written to Rout.f[0][t], Rout.f[4][t] (a field pair, or the adjoint's
 // slots).
-template <int CIJ, typename R, typename Out>
+template <int CIJ, typename R, typename Out, typename RowsT = NoRows>
 __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd, const Par& P, const Coef<R>& c,
                                          const CF<R>& ub, const CF<R>& ul, const CF<double>& un, const CF<double>& uk,
                                          const CF<R>& D, int hasD, const CF<double>& src, int has_src, R tau,
-                                         const Out& Rout, int i, int j, int k, int t) {
+                                         const Out& Rout, int i, int j, int k, int t, const RowsT& rows = RowsT()) {
   const auto Pp = ub.f[0];
   const auto UR = ub.f[1];
   const auto UT = ub.f[2];
@@ -280,11 +335,13 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
     else { uv[0] = vp<CIJ>(g, UP, i, j, k); uv[1] = vp<CIJ>(g, UP, i, j, k + 1); }
     RowC<R> w;
     row_c(g, P, c, d, 0, i, j, k, w);
+    rows_put_c(rows, d, 0, t, w);
     accp += w.wp[0] * pv[0] + w.wp[2] * pv[2] + w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2]
           + w.wv[0] * uv[0] + w.wv[1] * uv[1];
     if (d == 0) accp += w.adv * g.dbgp[i] - w.dif * g.lapT[i];
     ap = w.a;
     row_c(g, P, c, d, 1, i, j, k, w);
+    rows_put_c(rows, d, 1, t, w);
     accT += w.wT[0] * Tv[0] + w.wT[1] * Tv[1] + w.wT[2] * Tv[2] + w.wv[0] * uv[0] + w.wv[1] * uv[1];
     if (d == 0) accT += w.adv * g.dbgT[i] - w.dif * g.lapT[i];
     aT = w.a;
@@ -315,22 +372,27 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
 template <typename R, bool W>
 __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
                                                CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
-                                               int has_src, R tau, MF<R> Rout) {
+                                               int has_src, R tau, MF<R> Rout, Rows64 rows) {
   int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
       i = blockIdx.z * blockDim.z + threadIdx.z;
   bool inner = tile_inner(g) && !g.hasw;  // with wall data every tile takes the checked path
   if (k >= g.np || j >= g.nt || i >= g.nr) return;
   int t = IC(g, i, j, k);
-  if (inner) rhs_c_at<0>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
-  else rhs_c_at<W ? 2 : 1>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+  if constexpr (std::is_same<R, double>::value) {  // the FP64 mode stores its line rows
+    if (inner) rhs_c_at<0>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t, rows);
+    else rhs_c_at<W ? 2 : 1>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t, rows);
+  } else {
+    if (inner) rhs_c_at<0>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+    else rhs_c_at<W ? 2 : 1>(g, gd, P, c, ub, ul, un, uk, D, hasD, src, has_src, tau, Rout, i, j, k, t);
+  }
 }
 
 // R for the momentum row of component D on its faces: one thread per face
 // (zero on wall faces, which are not unknowns); written to Rout.f[1 + D][t].
-template <int CIJ, int D, typename R, typename Out>
+template <int CIJ, int D, typename R, typename Out, typename RowsT = NoRows>
 __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Coef<R>& c, const CF<R>& ub,
                                          const CF<R>& Dv, int hasD, const CF<double>& src, int has_src, R tau,
-                                         const Out& Rout, int i, int j, int k, int t) {
+                                         const Out& Rout, int i, int j, int k, int t, const RowsT& rows = RowsT()) {
   const auto Pp = ub.f[0];
   const auto UR = ub.f[1];
   const auto UT = ub.f[2];
@@ -340,11 +402,14 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
   R acc;
   if (D == 0) {
     row_f(g, P, c, UR, 0, i, j, k, wp, wu);
+    rows_put_f(rows, 0, t, wp, wu);
     acc = wp[1] * (cpert<CIJ>(g, Pp, i, j, k) - cpert<CIJ>(g, Pp, i - 1, j, k))
         + wu[0] * UR[IRf(g, i - 1, j, k)] + wu[1] * UR[t] + wu[2] * UR[IRf(g, i + 1, j, k)];
     row_s<CIJ>(g, P, c, ub, 0, 1, i, j, k, w);
+    rows_put_s(rows, 0, 1, t, w);
     acc += w[0] * vr<CIJ>(g, UR, i, j - 1, k) + w[1] * UR[t] + w[2] * vr<CIJ>(g, UR, i, j + 1, k);
     row_s<CIJ>(g, P, c, ub, 0, 2, i, j, k, w);
+    rows_put_s(rows, 0, 2, t, w);
     acc += w[0] * vr<CIJ>(g, UR, i, j, k - 1) + w[1] * UR[t] + w[2] * vr<CIJ>(g, UR, i, j, k + 1);
     // hydrostatic part: (1/rho_f) d p_ref/dr + g = (1 - b) e + g b, b = 1 - rho_ref,f / rho_f
     int c0 = IC(g, i - 1, j, k), c1 = IC(g, i, j, k);
@@ -368,11 +433,14 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
   } else if (D == 1) {
     R ir = g.irc[i];
     row_f(g, P, c, UT, 1, i, j, k, wp, wu);
+    rows_put_f(rows, 1, t, wp, wu);
     acc = wp[1] * (cpert<CIJ>(g, Pp, i, j, k) - cpert<CIJ>(g, Pp, i, j - 1, k))
         + wu[0] * UT[ITf(g, i, j - 1, k)] + wu[1] * UT[t] + wu[2] * UT[ITf(g, i, j + 1, k)];
     row_s<CIJ>(g, P, c, ub, 1, 0, i, j, k, w);
+    rows_put_s(rows, 1, 0, t, w);
     acc += w[0] * vt<CIJ>(g, UT, i - 1, j, k) + w[1] * UT[t] + w[2] * vt<CIJ>(g, UT, i + 1, j, k);
     row_s<CIJ>(g, P, c, ub, 1, 2, i, j, k, w);
+    rows_put_s(rows, 1, 2, t, w);
     acc += w[0] * vt<CIJ>(g, UT, i, j, k - 1) + w[1] * UT[t] + w[2] * vt<CIJ>(g, UT, i, j, k + 1);
     R isfj = g.isf[j], cfj = g.cf[j], cotf = g.cotf[j];
     R irh = sdiv(R(2), rho_at(g, c, i, j - 1, k) + rho_at(g, c, i, j, k));
@@ -396,11 +464,14 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
   } else {
     R ir = g.irc[i], is = g.isc[j], cot = g.cotc[j];
     row_f(g, P, c, UP, 2, i, j, k, wp, wu);
+    rows_put_f(rows, 2, t, wp, wu);
     acc = wp[1] * (cpert<CIJ>(g, Pp, i, j, k) - cpert<CIJ>(g, Pp, i, j, k - 1))
         + wu[0] * vp<CIJ>(g, UP, i, j, k - 1) + wu[1] * UP[t] + wu[2] * vp<CIJ>(g, UP, i, j, k + 1);
     row_s<CIJ>(g, P, c, ub, 2, 0, i, j, k, w);
+    rows_put_s(rows, 2, 0, t, w);
     acc += w[0] * vp<CIJ>(g, UP, i - 1, j, k) + w[1] * UP[t] + w[2] * vp<CIJ>(g, UP, i + 1, j, k);
     row_s<CIJ>(g, P, c, ub, 2, 1, i, j, k, w);
+    rows_put_s(rows, 2, 1, t, w);
     acc += w[0] * vp<CIJ>(g, UP, i, j - 1, k) + w[1] * UP[t] + w[2] * vp<CIJ>(g, UP, i, j + 1, k);
     R s = g.sc[j], cj = g.cc[j];
     R irh = sdiv(R(2), rho_at(g, c, i, j, k - 1) + rho_at(g, c, i, j, k));
@@ -431,7 +502,7 @@ __device__ __forceinline__ void rhs_u_at(const Geo<R>& g, const Par& P, const Co
 // one block per tile of faces; zero on wall faces, which are not unknowns
 template <typename R, int D, bool W>
 __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_u(Geo<R> g, Par P, Coef<R> c, CF<R> ub, CF<R> Dv, int hasD,
-                                               CF<double> src, int has_src, R tau, MF<R> Rout) {
+                                               CF<double> src, int has_src, R tau, MF<R> Rout, Rows64 rows) {
   int nj = g.nt + (D == 1), nk = D == 2 ? g.npf : g.np;
   int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
       i = blockIdx.z * blockDim.z + threadIdx.z;
@@ -440,8 +511,13 @@ __global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_u(Geo<R> g, Par P,
   int t = (i * nj + j) * nk + k;
   bool wall = D == 0 ? (i == 0 || i == g.nr) : D == 1 ? (j == 0 || j == g.nt) : (!g.per && (k == 0 || k == g.np));
   if (wall) { Rout.f[1 + D][t] = R(0); return; }
-  if (inner) rhs_u_at<0, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
-  else rhs_u_at<W ? 2 : 1, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+  if constexpr (std::is_same<R, double>::value) {  // the FP64 mode stores its line rows
+    if (inner) rhs_u_at<0, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t, rows);
+    else rhs_u_at<W ? 2 : 1, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t, rows);
+  } else {
+    if (inner) rhs_u_at<0, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+    else rhs_u_at<W ? 2 : 1, D>(g, P, c, ub, Dv, hasD, src, has_src, tau, Rout, i, j, k, t);
+  }
 }
 
 // ------------------------------------------------------------ line solvers
@@ -550,6 +626,7 @@ struct SweepArgs {
   int a0[3], nb[3], b0[3];
   double* acc;            // 5 sums of squares (mode 1)
   int* flag;
+  Rows64 rows;            // FP64 mode: the line rows the right-hand side stored
 };
 
 // Per-thread sums of squares of the increments, per field (the iteration
@@ -1072,7 +1149,40 @@ __device__ __forceinline__ void inv3_or_nan(const R* S, R* I, int* bad) {
   }
 }
 
-template <typename R, int D>
+// Block m of (I + h D_d) on a walled line from the stored rows: rc the 12 centre
+// values of the p- and T-rows, rf the 5 values of the normal-velocity row on
+// face m + 1 (m < n - 1); the same entries and wall folds as assemble_pts.
+template <typename R>
+__device__ __forceinline__ void assemble_rows(const R* rc, const R* rf, int n, int m, R h, R* A, R* B, R* C) {
+#pragma unroll
+  for (int q = 0; q < 9; q++) { A[q] = R(0); B[q] = R(0); C[q] = R(0); }
+  A[0] = h * rc[0]; A[1] = h * rc[2]; A[2] = h * rc[5];
+  B[1] = h * rc[3]; B[2] = h * rc[6];
+  C[0] = h * rc[1]; C[1] = h * rc[4];
+  A[4] = h * rc[7]; A[5] = h * rc[10];
+  B[4] = h * rc[8]; B[5] = h * rc[11];
+  C[4] = h * rc[9];
+  if (m < n - 1) {
+    A[8] = h * rf[2];
+    B[6] = h * rf[0]; B[8] = h * rf[3];
+    C[6] = h * rf[1]; C[8] = h * rf[4];
+  }
+  B[0] += R(1); B[4] += R(1); B[8] += R(1);
+  if (m == 0) {
+    B[0] += A[0]; B[1] += A[1]; B[3] += A[3]; B[4] += A[4];
+#pragma unroll
+    for (int q = 0; q < 9; q++) A[q] = R(0);
+  }
+  if (m == n - 1) {
+    B[0] += C[0]; B[1] += C[1]; B[3] += C[3]; B[4] += C[4];
+#pragma unroll
+    for (int q = 0; q < 9; q++) C[q] = R(0);
+    B[2] = R(0); B[5] = R(0);
+    A[8] = R(0); B[6] = R(0); B[7] = R(0); B[8] = R(1);
+  }
+}
+
+template <typename R, int D, bool ROWS>
 __device__ void block_line2(const SweepArgs<R>& S, int line, bool valid, int a, int b, int side, SqSum<R>& ss,
                             int* bad) {
   const Geo<R>& g = S.g;
@@ -1086,18 +1196,32 @@ __device__ void block_line2(const SweepArgs<R>& S, int line, bool valid, int a, 
   auto cell = [&](int s) { return side ? n - 1 - s : s; };
   CPt<R> cqn;
   FPt<R> fqn;
+  R rcn[ROWS ? 12 : 1], rfn[ROWS ? 5 : 1];
   R r0n = R(0), r4n = R(0), run = R(0);
   auto fetch = [&](int m) {
     int i, j, k, fi, fj, fk;
     line_pos(d, a, b, m, i, j, k);
     const int ic = IC(g, i, j, k);
-    cqn = load_c(S.c, d, ic);
-    fqn = {R(1), R(1), R(0)};
+    if constexpr (ROWS) {
+      const R* pc = S.rows.c[d] + ic;
+#pragma unroll
+      for (int q = 0; q < 12; q++) rcn[q] = pc[q * S.rows.nc];
+    } else {
+      cqn = load_c(S.c, d, ic);
+      fqn = {R(1), R(1), R(0)};
+    }
     run = R(0);
     if (m < n - 1) {
       next_face(d, n, m, i, j, k, fi, fj, fk);
-      fqn = load_f(g, S.c, S.ub.f[1 + d], d, fi, fj, fk);
-      run = S.rhs.f[1 + d][face_idx(g, d, fi, fj, fk)];
+      const int fx = face_idx(g, d, fi, fj, fk);
+      if constexpr (ROWS) {
+        const R* pf = S.rows.f[d] + fx;
+#pragma unroll
+        for (int q = 0; q < 5; q++) rfn[q] = pf[q * S.rows.nf[d]];
+      } else {
+        fqn = load_f(g, S.c, S.ub.f[1 + d], d, fi, fj, fk);
+      }
+      run = S.rhs.f[1 + d][fx];
     }
     r0n = S.rhs.f[0][ic];
     r4n = S.rhs.f[4][ic];
@@ -1112,13 +1236,23 @@ __device__ void block_line2(const SweepArgs<R>& S, int line, bool valid, int a, 
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
     R A[9], B[9], C[9];
-    const CPt<R> cq = cqn;
-    const FPt<R> fq = fqn;
     R rr[3] = {r0n, r4n, run};
-    if (s + 1 < cnt) fetch(cell(s + 1));
-    int fi, fj, fk;
-    next_face(d, n, m, i, j, k, fi, fj, fk);
-    assemble_pts(g, S.P, cq, fq, d, n, 0, m, i, j, fi, fj, S.h, A, B, C);
+    if constexpr (ROWS) {
+      R rc[12], rf[5];
+#pragma unroll
+      for (int q = 0; q < 12; q++) rc[q] = rcn[q];
+#pragma unroll
+      for (int q = 0; q < 5; q++) rf[q] = rfn[q];
+      if (s + 1 < cnt) fetch(cell(s + 1));
+      assemble_rows(rc, rf, n, m, S.h, A, B, C);
+    } else {
+      const CPt<R> cq = cqn;
+      const FPt<R> fq = fqn;
+      if (s + 1 < cnt) fetch(cell(s + 1));
+      int fi, fj, fk;
+      next_face(d, n, m, i, j, k, fi, fj, fk);
+      assemble_pts(g, S.P, cq, fq, d, n, 0, m, i, j, fi, fj, S.h, A, B, C);
+    }
     // L couples to the cell already eliminated, U to the next one
     R L[9], U[9];
 #pragma unroll
@@ -1219,7 +1353,7 @@ __device__ void block_line2(const SweepArgs<R>& S, int line, bool valid, int a, 
 
 // The scalar (transverse-component) lines the same way: Thomas from both ends,
 // (1 - e_o e_p) x_o = g_o - e_o g_p at the meeting cells.
-template <typename R, int D, int KIND>
+template <typename R, int D, int KIND, bool ROWS>
 __device__ void scalar_line2(const SweepArgs<R>& S, int line, bool valid, int a, int b, int side, SqSum<R>& ss,
                              int* bad) {
   const Geo<R>& g = S.g;
@@ -1233,12 +1367,20 @@ __device__ void scalar_line2(const SweepArgs<R>& S, int line, bool valid, int a,
   const int cnt = side ? n - h : h;
   auto cell = [&](int s) { return side ? n - 1 - s : s; };
   SPt<R> qn;
+  R wn[3];
   R rn = R(0);
   auto fetch = [&](int m) {
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    qn = load_s<2>(g, S.c, S.ub, cc, d, i, j, k);
-    rn = rhs[face_idx(g, cc, i, j, k)];
+    const int fx = face_idx(g, cc, i, j, k);
+    if constexpr (ROWS) {
+      const long nfc = S.rows.nf[cc];
+      const R* ps = S.rows.s[cc] + 3 * trans_slot(cc, d) * nfc + fx;
+      wn[0] = ps[0]; wn[1] = ps[nfc]; wn[2] = ps[2 * nfc];
+    } else {
+      qn = load_s<2>(g, S.c, S.ub, cc, d, i, j, k);
+    }
+    rn = rhs[fx];
   };
   R e = R(0), gy = R(0);
   if (cnt > 0) fetch(cell(0));
@@ -1246,11 +1388,16 @@ __device__ void scalar_line2(const SweepArgs<R>& S, int line, bool valid, int a,
     const int m = cell(s);
     int i, j, k;
     line_pos(d, a, b, m, i, j, k);
-    const SPt<R> q = qn;
     const R r = rn;
-    if (s + 1 < cnt) fetch(cell(s + 1));
     R w[3];
-    row_sw(g, S.P, q, cc, d, i, j, w);
+    if constexpr (ROWS) {
+      w[0] = wn[0]; w[1] = wn[1]; w[2] = wn[2];
+      if (s + 1 < cnt) fetch(cell(s + 1));
+    } else {
+      const SPt<R> q = qn;
+      if (s + 1 < cnt) fetch(cell(s + 1));
+      row_sw(g, S.P, q, cc, d, i, j, w);
+    }
     R am = S.h * w[0], bm = R(1) + S.h * w[1], cm = S.h * w[2];
     if (m == 0) { bm -= am; am = R(0); }
     if (m == n - 1) { bm -= cm; cm = R(0); }
@@ -1294,7 +1441,7 @@ __device__ void scalar_line2(const SweepArgs<R>& S, int line, bool valid, int a,
 }
 
 // one warp per 16 lines of one kind (blockIdx.y): lanes l and l + 16 share a line
-template <typename R, int D>
+template <typename R, int D, bool ROWS>
 __global__ void __launch_bounds__(128) k_sweep2(SweepArgs<R> S) {
   const int kind = blockIdx.y;
   const int nl = S.nl[kind];
@@ -1309,9 +1456,9 @@ __global__ void __launch_bounds__(128) k_sweep2(SweepArgs<R> S) {
   int bad = 0;
   int a = (int)(line / S.nb[kind]) + S.a0[kind];
   int b = (int)(line % S.nb[kind]) + S.b0[kind];
-  if (kind == 0) block_line2<R, D>(S, line, valid, a, b, side, ss, &bad);
-  else if (kind == 1) scalar_line2<R, D, 1>(S, line, valid, a, b, side, ss, &bad);
-  else scalar_line2<R, D, 2>(S, line, valid, a, b, side, ss, &bad);
+  if (kind == 0) block_line2<R, D, ROWS>(S, line, valid, a, b, side, ss, &bad);
+  else if (kind == 1) scalar_line2<R, D, 1, ROWS>(S, line, valid, a, b, side, ss, &bad);
+  else scalar_line2<R, D, 2, ROWS>(S, line, valid, a, b, side, ss, &bad);
   if (bad) atomicOr(S.flag, bad);
   if (S.update) {
     for (int f = 0; f < 5; f++) {

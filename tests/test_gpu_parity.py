@@ -139,6 +139,27 @@ def test_sweep_parity_fp64_both_line_forms(name, d):
         assert rel_err(out[sph.SPH_LINES_PARTITIONED][q], out[sph.SPH_LINES_THOMAS][q]) <= 1e-12, (name, d, q)
 
 
+@pytest.mark.parametrize("name", ["sector", "bubble", "ragged", "shell_pole"])
+def test_step_fp64_stored_rows_vs_formed_rows(name):
+    """FP64 steps: the sweeps reading the line rows the right-hand side stored
+    (the default) against the sweeps forming every row themselves
+    (SPH_LINES_THOMAS), both within 1e-10 of the oracle; on the periodic shell
+    the r and theta sweeps read stored rows and the cyclic phi lines form theirs."""
+    g, par, bg, Un, Uk, S, dt = CASES[name]()
+    ref, _ = oracle.step(g, par, Un, dt, 2, bg=bg, S=S)
+    out = {}
+    for which in (sph.SPH_LINES_THOMAS, sph.SPH_LINES_PARTITIONED):
+        s = solver_for(g, par, bg, Un)
+        s.set_line_solver(which)
+        s.step(dt, 2, S)
+        out[which] = to_host(s.get_state())
+        s.close()
+        for q in range(5):
+            assert rel_err(out[which][q], ref[q]) <= 1e-10, (name, which, q, rel_err(out[which][q], ref[q]))
+    for q in range(5):
+        assert rel_err(out[sph.SPH_LINES_PARTITIONED][q], out[sph.SPH_LINES_THOMAS][q]) <= 1e-11, (name, q)
+
+
 def _steps(g, par, bg, U0, dt, K, nsteps, source=None):
     s = solver_for(g, par, bg, U0)
     Uo = U0
