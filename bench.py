@@ -38,9 +38,10 @@ UNIT = "points/s"
 
 # FP64 operations (DADD + DMUL + 2 DFMA, counted from the kernels' SASS
 # instruction mix with ncu, profiles/fp64_counts_bubble_64cubed.md) per grid
-# point of one K = 2 step of the FP64 mode: 2 x (911 right-hand side + 158
-# coefficients + 1381 sweeps) + 15 (the second iteration's average).
-FP64_FLOP_PER_POINT_STEP = 4915.0
+# point of one K = 2 step of the FP64 mode: 2 x (1000 right-hand side, which
+# also stores the line rows + 158 coefficients + 834 sweeps, which read them)
+# + 15 (the second iteration's average).
+FP64_FLOP_PER_POINT_STEP = 4000.0
 # FP64 FMA throughput of GB300 measured on this machine with independent FMA
 # chains (152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz); MEASURED_PEAKS.json has no
 # FP64 figure, so this is the library's own measurement.
@@ -81,9 +82,9 @@ MIXED_BYTES_PER_POINT = {"sweep_r": 60, "sweep_theta": 60, "sweep_phi": 120, "rh
 # count; the sweeps only where their line layouts are the same (theta and phi
 # lines of 256 cells; the window's r lines are 64 cells, the workload's 128).
 TRAFFIC_GRID = (64, 256, 256)
-MEASURED_TRAFFIC = {"avg": 92.4, "coef": 75.3, "rhs": 198.6, "sweep_theta": 70.2, "sweep_phi": 130.4}
+MEASURED_TRAFFIC = {"avg": 92.6, "coef": 75.4, "rhs": 199.0, "sweep_theta": 68.6, "sweep_phi": 130.6}
 PER_POINT_STAGES = ("avg", "coef", "rhs", "sweep_theta", "sweep_phi")
-TRAFFIC_SOURCE_HASH = "6b0c21b233c25195"
+TRAFFIC_SOURCE_HASH = "8343889b4a6ba17a"
 
 
 def kernel_source_hash():
@@ -335,7 +336,7 @@ def run_ours(args, rank, world, dist):
                              "peak": FP64_PEAK_TFLOPS, "frac": ach64 / FP64_PEAK_TFLOPS,
                              "peak_source": "FP64 FMA rate measured by this library on the pool's GB300 "
                                             "(MEASURED_PEAKS.json has no FP64 figure)",
-                             "hbm_note": "the FP64 step does ~4900 FP64 flop per point against ~1 KB of traffic: "
+                             "hbm_note": "the FP64 step does ~4000 FP64 flop per point against ~2.5 KB of traffic: "
                                          "bound by the FP64 pipe, not HBM"}}
 
     # dominant kernel of the mixed step and its HBM roofline

@@ -368,9 +368,14 @@ __device__ __forceinline__ void rhs_c_at(const Geo<R>& g, const Geo<double>& gd,
   Rout.f[4][t] = -d4 - tau * NT;
 }
 
-// one block per tile
+// one block per tile.  FP64: at least SPH_RHSC64_MINB blocks of 128 threads
+// per SM (the compiler would otherwise take ~190 registers a thread for the
+// centre rows it keeps live until their stores, leaving two blocks per SM).
+#ifndef SPH_RHSC64_MINB
+#define SPH_RHSC64_MINB 4
+#endif
 template <typename R, bool W>
-__global__ void __launch_bounds__(128, STENCIL_MINB(R)) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? STENCIL_MINB(R) : SPH_RHSC64_MINB) k_rhs_c(Geo<R> g, Geo<double> gd, Par P, Coef<R> c, CF<R> ub, CF<R> ul,
                                                CF<double> un, CF<double> uk, CF<R> D, int hasD, CF<double> src,
                                                int has_src, R tau, MF<R> Rout, Rows64 rows) {
   int k = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
